@@ -1,0 +1,135 @@
+"""Gaussian and derivative-Gaussian kernels, their regularisation and their
+discrete Fourier coefficients, FP64. Test infrastructure only.
+
+Kernels (Sec. 3.3, eqs. "implement_gaussian_kernel" and
+"implement_der_gaussian_kernel", with c = sqrt(2) ell):
+
+    kappa_gauss(r) = exp(-r^2 / c^2)
+    kappa_der(r)   = (r^2 / c^2) exp(-r^2 / c^2)
+
+so that K v = sigma_f^2 sum_s K_s^gauss v and dK/d ell_s v = sigma_f^2 (2/ell_s) K_s^der v.
+
+Regularisation (Sec. 3.1: the kernel is periodised by "a smooth transition" at
+the edges, after Potts-Steidl; the paper does not write it down). Reading: with
+a = 1/2 - eps_B the regularised radial profile is
+
+    K_R(r) = kappa(r)           r <= a
+           = T(r)               a < r <= 1/2
+           = kappa(1/2)         r > 1/2 (inside the cube [-1/2,1/2]^d)
+
+where T is the polynomial of degree 2p-1 with T^(j)(a) = kappa^(j)(a) for
+j < p, T(1/2) = kappa(1/2) and T^(j)(1/2) = 0 for 1 <= j < p. p = 0 means no
+regularisation at all: K_R = kappa on the whole cube, i.e. the plain periodic
+continuation that the error theorems of Sec. 3.4 assume.
+
+Discrete Fourier coefficients (Lemma "aliasing error", Sec. 3.4):
+
+    c_hat_k = M^-d sum_{j in I_M} K_R(||j/M||) exp(-2 pi i j.k / M),   k in I_M,
+    I_M = {-M/2, ..., M/2-1}^d.
+"""
+from __future__ import annotations
+
+from math import factorial
+
+import numpy as np
+from numpy.polynomial.hermite import hermval
+
+
+def kappa(r, ell: float, kind: str = "gauss"):
+    """kind='gauss': exp(-r^2/c^2); kind='der': (r^2/c^2) exp(-r^2/c^2); c = sqrt(2) ell."""
+    r = np.asarray(r, dtype=np.float64)
+    q = r * r / (2.0 * ell * ell)
+    e = np.exp(-q)
+    return e if kind == "gauss" else q * e
+
+
+def radial_derivatives(r0: float, ell: float, p: int, kind: str = "gauss"):
+    """d^j/dr^j kappa(r) at r0 for j = 0..p-1.
+
+    Gaussian: d^j/dr^j exp(-(r/c)^2) = (-1/c)^j H_j(r/c) exp(-(r/c)^2), H_j the
+    physicists' Hermite polynomials. Derivative kernel: Leibniz rule on
+    (r/c)^2 * exp(-(r/c)^2)."""
+    c = np.sqrt(2.0) * ell
+    x = r0 / c
+    g = []
+    for j in range(p + 2):
+        coef = np.zeros(j + 1)
+        coef[j] = 1.0
+        g.append((-1.0 / c) ** j * hermval(x, coef) * np.exp(-x * x))
+    g = np.array(g)
+    if kind == "gauss":
+        return g[:p]
+    q = [r0 * r0 / c ** 2, 2.0 * r0 / c ** 2, 2.0 / c ** 2]   # (r/c)^2 and its derivatives
+    out = []
+    for j in range(p):
+        s = 0.0
+        for i in range(0, min(j, 2) + 1):
+            s += factorial(j) / (factorial(i) * factorial(j - i)) * q[i] * g[j - i]
+        out.append(s)
+    return np.array(out)
+
+
+def transition_polynomial(ell: float, p: int, eps_B: float, kind: str = "gauss"):
+    """Coefficients t_0..t_{2p-1} of T(r) = sum_i t_i (r - a)^i (see module docstring)."""
+    a = 0.5 - eps_B
+    h = 0.5 - a
+    da = radial_derivatives(a, ell, p, kind)
+    vb = float(kappa(0.5, ell, kind))
+    n = 2 * p
+    A = np.zeros((n, n))
+    rhs = np.zeros(n)
+    for j in range(p):                  # T^(j)(a) = kappa^(j)(a)
+        A[j, j] = factorial(j)
+        rhs[j] = da[j]
+    for j in range(p):                  # T(1/2) = kappa(1/2), T^(j)(1/2) = 0 for j >= 1
+        for i in range(j, n):
+            A[p + j, i] = factorial(i) / factorial(i - j) * h ** (i - j)
+        rhs[p + j] = vb if j == 0 else 0.0
+    return np.linalg.solve(A, rhs)
+
+
+def regularised(r, ell: float, p: int, eps_B: float, kind: str = "gauss"):
+    """K_R(r) of the module docstring; p = 0 returns kappa itself."""
+    r = np.asarray(r, dtype=np.float64)
+    if p == 0:
+        return kappa(r, ell, kind)
+    a = 0.5 - eps_B
+    t = transition_polynomial(ell, p, eps_B, kind)
+    T = np.polynomial.polynomial.polyval(r - a, t)
+    vb = float(kappa(0.5, ell, kind))
+    return np.where(r <= a, kappa(r, ell, kind), np.where(r <= 0.5, T, vb))
+
+
+def default_p(M: int, eps_B: float) -> int:
+    """Regularisation degree used when none is given: about the number of coefficient-grid
+    samples that fall in the transition band, round(M eps_B), at least 1."""
+    return max(1, int(round(M * eps_B)))
+
+
+def coefficients(ell: float, d: int, M: int, p: int, eps_B: float, kind: str = "gauss"):
+    """c_hat_k for k in I_M^d, as a real array of shape (M,)*d indexed by k + M/2.
+
+    Samples K_R at j/M, j in I_M^d, then the d-dimensional DFT (Lemma "aliasing
+    error"). The imaginary part vanishes because K_R is even; it is dropped."""
+    j = np.arange(-M // 2, M // 2) / M
+    grids = np.meshgrid(*([j] * d), indexing="ij")
+    r = np.sqrt(sum(g * g for g in grids))
+    samples = regularised(r, ell, p, eps_B, kind)
+    c = np.fft.fftn(np.fft.ifftshift(samples)) / M ** d
+    return np.fft.fftshift(c).real
+
+
+def trig_poly_eval(chat: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """K_F(r) = sum_{k in I_M^d} c_hat_k exp(2 pi i k.r) at points r (npts x d)."""
+    d = chat.ndim
+    M = chat.shape[0]
+    k = np.arange(-M // 2, M // 2)
+    E = [np.exp(2j * np.pi * np.outer(r[:, t], k)) for t in range(d)]
+    if d == 1:
+        return (E[0] @ chat).real
+    if d == 2:
+        return np.einsum("na,ab,nb->n", E[0], chat, E[1]).real
+    tmp = chat.reshape(M * M, M) @ E[2].T           # (a b) x n
+    tmp = tmp.reshape(M, M, -1)
+    tmp = np.einsum("abn,nb->an", tmp, E[1])
+    return np.einsum("an,na->n", tmp, E[0]).real

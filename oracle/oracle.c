@@ -1,0 +1,185 @@
+/*
+ * FP64 CPU oracle, C part. TEST INFRASTRUCTURE ONLY: tests, the smoke check and
+ * the benchmark's CPU-baseline leg call this code; the product path never does.
+ *
+ * Plain loops, no blocking, no tricks. Every function states the formula it
+ * follows (Wagner, Nestler, Stoll, "Fast Evaluation of Additive Kernels").
+ *
+ *  orc_direct   : the additive Gaussian kernel product K v and the length-scale
+ *                 derivative products dK/d(ell_s) v, straight from their
+ *                 definitions (Sec. 3.3, eq. "add_gauss_kernel" and the
+ *                 dK_ij/d ell formula right after it), for a chosen set of rows.
+ *  orc_spread   : the spreading step of the adjoint NFFT,
+ *                 g_l = sum_j v_j phi~(x_j - l/n), l in I_n^D (Sec. 3.1, the
+ *                 inner sum of eq. "approx fast sum" computed approximately).
+ *  orc_gather   : the interpolation step of the NFFT,
+ *                 f_i = sum_l h_l phi~(x_i - l/n) (Sec. 3.1, the outer sum).
+ *
+ * phi is the Kaiser-Bessel window with shape b and cutoff m on a grid of n
+ * points per dimension:
+ *   phi(x) = sinh(b*sqrt(m^2 - (n x)^2)) / (pi * sqrt(m^2 - (n x)^2)),  |n x| <= m,
+ * zero outside; phi~ is its 1-periodisation. Grid index l runs over
+ * -n/2 .. n/2-1 and is stored at array position l + n/2 (wrapped mod n).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static const double ORC_PI = 3.14159265358979323846;
+
+/* Kaiser-Bessel window as a function of t = n*x (grid units). */
+static double kb(double t, int m, double b)
+{
+    double s2 = (double)m * (double)m - t * t;
+    if (s2 < 0.0) return 0.0;
+    double s = sqrt(s2);
+    if (s < 1e-8) return b / ORC_PI;           /* limit of sinh(b s)/s as s -> 0 */
+    return sinh(b * s) / (ORC_PI * s);
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/*
+ * Direct sums for rows[0..nrows).
+ *   Kv[r]          = sigma_f^2 sum_s sum_j exp(-|x_i^W - x_j^W|^2 / (2 ell_s^2)) v_j
+ *   dK[s*nrows+r]  = sigma_f^2 sum_j |x_i^W - x_j^W|^2 / ell_s^3 * exp(...) v_j
+ * X is N x d row-major float32 (the same numbers the GPU sees), promoted to double.
+ * Windows are CSR: features of window s are win_feat[win_off[s] .. win_off[s+1]).
+ */
+void orc_direct(int64_t N, int d, const float *X, int P, const int *win_off, const int *win_feat,
+                const double *ell, double sigma_f, const double *v, int64_t nrows,
+                const int64_t *rows, double *Kv, double *dK)
+{
+    (void)d;
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t r = 0; r < nrows; ++r) {
+        int64_t i = rows[r];
+        double ksum = 0.0;
+        for (int s = 0; s < P; ++s) {
+            double e2 = 2.0 * ell[s] * ell[s];
+            double l3 = ell[s] * ell[s] * ell[s];
+            double ks = 0.0, ds = 0.0;
+            for (int64_t j = 0; j < N; ++j) {
+                double r2 = 0.0;
+                for (int q = win_off[s]; q < win_off[s + 1]; ++q) {
+                    int f = win_feat[q];
+                    double diff = (double)X[i * d + f] - (double)X[j * d + f];
+                    r2 += diff * diff;
+                }
+                double k = exp(-r2 / e2);
+                ks += k * v[j];
+                ds += r2 / l3 * k * v[j];
+            }
+            ksum += ks;
+            dK[(int64_t)s * nrows + r] = sigma_f * sigma_f * ds;
+        }
+        Kv[r] = sigma_f * sigma_f * ksum;
+    }
+}
+
+/* Support of phi~(x - l/n) along one axis: l = floor(n x) - m + 1 + t, t = 0..2m-1. */
+static void support(double x, int n, int m, double b, int64_t *idx, double *w)
+{
+    double u = x * n;
+    double fl = floor(u);
+    for (int t = 0; t < 2 * m; ++t) {
+        double l = fl - m + 1 + t;
+        w[t] = kb(u - l, m, b);
+        int64_t a = ((int64_t)l + n / 2) % n;
+        if (a < 0) a += n;
+        idx[t] = a;
+    }
+}
+
+/*
+ * Spreading (adjoint NFFT, first step): g[a] += v_j * prod_t phi~(x_{j,t} - l_t/n)
+ * for the 2m^D grid points around x_j. x is N x D row-major double in [-1/2,1/2).
+ * g has n^D entries, index ((a0*n)+a1)*n+a2 for D = 3 (last axis fastest).
+ * Threads spread disjoint point ranges into private grids that are summed at the end.
+ */
+void orc_spread(int64_t N, int D, const double *x, const double *v, int n, int m, double b, double *g)
+{
+    int64_t G = 1;
+    for (int t = 0; t < D; ++t) G *= n;
+    memset(g, 0, sizeof(double) * (size_t)G);
+    int nth = orc_num_threads();
+    double *priv = (double *)calloc((size_t)nth * (size_t)G, sizeof(double));
+    #pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *mine = priv + (size_t)tid * (size_t)G;
+        int64_t idx[3][64];
+        double w[3][64];
+        #pragma omp for schedule(static)
+        for (int64_t j = 0; j < N; ++j) {
+            for (int t = 0; t < D; ++t) support(x[j * D + t], n, m, b, idx[t], w[t]);
+            int W = 2 * m;
+            if (D == 1) {
+                for (int a = 0; a < W; ++a) mine[idx[0][a]] += v[j] * w[0][a];
+            } else if (D == 2) {
+                for (int a = 0; a < W; ++a)
+                    for (int c = 0; c < W; ++c)
+                        mine[idx[0][a] * n + idx[1][c]] += v[j] * w[0][a] * w[1][c];
+            } else {
+                for (int a = 0; a < W; ++a)
+                    for (int c = 0; c < W; ++c)
+                        for (int e = 0; e < W; ++e)
+                            mine[(idx[0][a] * n + idx[1][c]) * n + idx[2][e]] +=
+                                v[j] * w[0][a] * w[1][c] * w[2][e];
+            }
+        }
+    }
+    for (int t = 0; t < nth; ++t)
+        for (int64_t a = 0; a < G; ++a) g[a] += priv[(size_t)t * (size_t)G + a];
+    free(priv);
+}
+
+/*
+ * Interpolation (NFFT, last step): out[i] = sum over the 2m^D grid points around x_i
+ * of h[a] * prod_t phi~(x_{i,t} - l_t/n). nh grids are read (h is nh x n^D).
+ * out is nh x N.
+ */
+void orc_gather(int64_t N, int D, const double *x, int n, int m, double b, int nh, const double *h,
+                double *out)
+{
+    int64_t G = 1;
+    for (int t = 0; t < D; ++t) G *= n;
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t idx[3][64];
+        double w[3][64];
+        for (int t = 0; t < D; ++t) support(x[i * D + t], n, m, b, idx[t], w[t]);
+        int W = 2 * m;
+        for (int q = 0; q < nh; ++q) {
+            const double *hq = h + (size_t)q * (size_t)G;
+            double s = 0.0;
+            if (D == 1) {
+                for (int a = 0; a < W; ++a) s += hq[idx[0][a]] * w[0][a];
+            } else if (D == 2) {
+                for (int a = 0; a < W; ++a)
+                    for (int c = 0; c < W; ++c)
+                        s += hq[idx[0][a] * n + idx[1][c]] * w[0][a] * w[1][c];
+            } else {
+                for (int a = 0; a < W; ++a)
+                    for (int c = 0; c < W; ++c)
+                        for (int e = 0; e < W; ++e)
+                            s += hq[(idx[0][a] * n + idx[1][c]) * n + idx[2][e]] * w[0][a] * w[1][c] * w[2][e];
+            }
+            out[(size_t)q * (size_t)N + i] = s;
+        }
+    }
+}
