@@ -1,0 +1,331 @@
+"""Benchmark: fused additive-kernel products K v + dK/d ell_s v (all s) per second on GB300.
+
+One step = one fused product (addker_matvec_all) on the workload: N = 1e6 points, d = 9, three windows
+of 3 consecutive features, ell = (0.3, 0.5, 1.0), sigma_f = 1, bandwidth M = 32, oversampling 2,
+cutoff m = 4 (N(0,1) features scaled into the ball of radius 1/4 - eps_B/2; synthetic, seeded).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--N 1000000]
+
+--gpus N > 1 runs under torchrun, one rank per GPU: independent replicas (the product needs no
+exchange between GPUs at this size), weak scaling; value = all ranks' units / max-over-ranks time.
+--impl reference times the FP64 CPU oracle (the plain NFFT fast sum) on the host cores instead.
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "additive K·v + dK/d(ell)·v per sec, N=1M, 3x3 windows, err<=1e-4 vs FP64"
+UNIT = "units/s"   # one unit = K v plus dK/d ell_s v for every window s (dK/d sigma_f v = (2/sigma_f) K v is free)
+SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def workload_desc(N):
+    return {"workload": f"c1-shaped at N={N}: d=9, windows (0,1,2),(3,4,5),(6,7,8), ell=(0.3,0.5,1.0), "
+                        "sigma_f=1, M=32, sigma=2, m=4, p=2, eps_B=1/16, N(0,1) features scaled into the ball",
+            "N": N, "d": 9, "P": 3, "bandwidth": 32, "cutoff": 4, "nrhs": 1,
+            "l2": "flushed between timed steps (write of a 512 MB buffer)"}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        self.file.flush()
+        rows = []
+        try:
+            with open(self.file.name) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except Exception:
+            pass
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_step(wl, v, sample_N):
+    """One oracle fused product on the first sample_N points (all windows); returns seconds."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.fastsum.matvec_all(wl.points[:sample_N], wl.windows, wl.ell, wl.sigma_f, v[:sample_N],
+                              wl.bandwidth, wl.cutoff)
+    return time.perf_counter() - t0
+
+
+def cpu_cores():
+    import oracle
+    from oracle import _clib
+    return int(_clib.lib().orc_num_threads())
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle on the host cores: each step is the oracle's fused product on a bounded
+    sample of the workload; units/s scaled by sample/N (the oracle's cost is linear in N up to the
+    N-independent coefficient and FFT work, which this scaling charges in full)."""
+    if rank != 0:
+        return
+    import workloads
+    wl = workloads.make("c1", N=args.N)
+    v = wl.vector()
+    sample = min(args.N, args.ref_sample)
+    for _ in range(args.warmup):
+        cpu_oracle_step(wl, v, sample)
+    ts = [cpu_oracle_step(wl, v, sample) for _ in range(args.steps)]
+    sec = sum(ts) / len(ts) * (args.N / sample)
+    val = 1.0 / sec
+    cores = cpu_cores()
+    out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_desc(args.N),
+           "impl": "reference",
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"first {sample} of {args.N} points, all 3 windows, scaled by N/sample"},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import workloads
+    __graft_entry__.build()
+    from paper_2404_17344_gb300 import AddKer
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl", device_id=dev)
+        dist = dist_mod
+
+    wl = workloads.make("c1", N=args.N)
+    v_np = wl.vector()
+    pts = torch.from_numpy(wl.points).to(dev)
+    v = torch.from_numpy(v_np).to(dev)
+    t0 = time.perf_counter()
+    op = AddKer(pts, wl.windows, wl.ell, wl.sigma_f, wl.bandwidth, wl.cutoff)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    N, P = wl.N, wl.P
+    Kv = torch.empty(N, device=dev)
+    dK = torch.empty(P * N, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, device=dev)
+
+    for _ in range(args.warmup):
+        op.matvec_all(v, Kv, dK)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    op.profile(True)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local_rank)
+    with ClockSampler(gpu_id) as clk:
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            op.matvec_all(v, Kv, dK)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    stage = op.profile_read()
+    op.profile(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+
+    # end to end through the host-buffer entry point: pinned host v in, Kv and dK out, copies timed
+    vh = torch.from_numpy(v_np).pin_memory()
+    Kh = torch.empty(N).pin_memory()
+    dKh = torch.empty(N * P).pin_memory()
+    for _ in range(2):
+        op.matvec_all_host(vh, Kh, dKh)
+    e2e_ts = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        op.matvec_all_host(vh, Kh, dKh)
+        e2e_ts.append(time.perf_counter() - t0)
+    e2e_sec = sum(e2e_ts) / len(e2e_ts)
+    if dist:
+        t = torch.tensor([e2e_sec], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_sec = float(t.item())
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (spread or gather): FP32 FMA pipe, algorithmic flops per launch
+    pk, pk_kind = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12          # TFLOP/s
+    W3 = (2 * wl.cutoff) ** 3
+    flops = {"spread": 2.0 * W3 * N * P, "gather": 2.0 * 2 * W3 * N * P}     # per launch (all windows)
+    dom = max(("spread", "gather"), key=lambda k: stage[k][0])
+    dom_ms, dom_launches = stage[dom]
+    per_launch_s = dom_ms / 1e3 / max(1, dom_launches)
+    achieved = flops[dom] / per_launch_s / 1e12
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", f"{dom}_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    # algorithmic HBM bytes per unit: coordinates read twice (36 B each), v (4 B), outputs 4(1+P) B per point
+    hbm_bytes = N * (2 * 4 * wl.d + 4 + 4 * (1 + P))
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+
+    # CPU oracle baseline, bounded sample
+    sample = min(N, args.cpu_sample)
+    cpu_sec = cpu_oracle_step(wl, v_np, sample) * (N / sample)
+
+    # accuracy on sampled rows against the FP64 CPU NFFT (same settings) and the FP64 direct sum
+    acc = None
+    if not args.no_check:
+        import oracle
+        rows = np.random.default_rng(0).choice(N, args.check_rows, replace=False)
+        Kn, dKn = oracle.fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f, v_np.astype(np.float64),
+                                            wl.bandwidth, wl.cutoff, rows=rows)
+        Kd, dKd = oracle.fastsum.direct(wl.points, wl.windows, wl.ell, wl.sigma_f, v_np.astype(np.float64),
+                                        rows=rows)
+        Kg = Kv.cpu().numpy()[rows]
+        dg = dK.reshape(P, N).cpu().numpy()[:, rows]
+        r = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        acc = {"rows": int(args.check_rows),
+               "Kv_vs_fp64_nfft": r(Kg, Kn), "dK_vs_fp64_nfft": [r(dg[s], dKn[s]) for s in range(P)],
+               "Kv_vs_fp64_direct": r(Kg, Kd), "dK_vs_fp64_direct": [r(dg[s], dKd[s]) for s in range(P)],
+               "oracle_nfft_Kv_vs_direct": r(Kn, Kd),
+               "oracle_nfft_dK_vs_direct": [r(dKn[s], dKd[s]) for s in range(P)]}
+
+    launches = int(sum(c for _, c in stage.values()))
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_desc(N),
+           "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                        "frac": achieved / fp32_peak, "traffic": traffic,
+                        "peak_source": f"FP32 FMA pipe: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz "
+                                       f"(sm_max_mhz {pk_kind})"},
+           "roofline_hbm": {"achieved": hbm_bytes / (ms_per_step / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": hbm_bytes / (ms_per_step / 1e3) / 1e9 / hbm_peak,
+                            "note": f"algorithmic bytes of the whole step, {pk_kind} copy bandwidth"},
+           "stage_ms_per_step": {k: t / args.steps for k, (t, _) in stage.items()},
+           "cpu_baseline": {"value": 1.0 / cpu_sec, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                            "sample": f"oracle CPU NFFT fused product on the first {sample} of {N} points, "
+                                      f"time scaled by N/sample"},
+           "e2e": {"value": world / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": 4 * N,
+                   "d2h_bytes_per_step": 4 * N * (1 + P)},
+           "gpu_launches": launches * 1,
+           "gpu_launches_per_step": launches / args.steps,
+           "clocks": clk.summary(), "setup_ms": setup_ms, "wall_s_timed": wall,
+           "accuracy": acc}
+    print(json.dumps(out), flush=True)
+    op.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=1_000_000)
+    ap.add_argument("--cpu-sample", type=int, default=200_000)
+    ap.add_argument("--ref-sample", type=int, default=100_000)
+    ap.add_argument("--check-rows", type=int, default=256)
+    ap.add_argument("--no-check", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * addker.h - C ABI of the GB300 library for NFFT-based products with additive
+ * Gaussian kernels and their hyperparameter derivatives.
+ *
+ * Operation (Wagner, Nestler, Stoll, "Fast Evaluation of Additive Kernels",
+ * arXiv 2404.17344):
+ *
+ *   K v              = sigma_f^2 sum_{s=1}^{P} K_s v,
+ *   (K_s)_{ij}       = exp(-||x_i^{W_s} - x_j^{W_s}||^2 / (2 ell_s^2))
+ *                      (Sec. 1 eq. "wind_gauss_anova_kernel", Sec. 3.3 eq. "add_gauss_kernel"),
+ *   dK/d ell_s v     = sigma_f^2 (2/ell_s) K_s^der v,
+ *   (K_s^der)_{ij}   = (r^2/(2 ell_s^2)) exp(-r^2/(2 ell_s^2)),  r = ||x_i^{W_s} - x_j^{W_s}||
+ *                      (Sec. 3.3 eq. "implement_der_gaussian_kernel" with c = sqrt(2) ell),
+ *   dK/d sigma_f v   = (2/sigma_f) K v                          (Sec. 3.3),
+ *
+ * each K_s v and K_s^der v approximated by the NFFT fast summation of Sec. 3.1
+ * (eq. "approx fast sum"): spreading onto an oversampled grid (adjoint NFFT),
+ * FFT, multiplication by the Fourier coefficients of the regularised kernel
+ * (Lemma "aliasing error": coefficients from M^{d_s} samples), inverse FFT,
+ * interpolation (NFFT). Every step of a product runs in CUDA kernels on the
+ * device; FP32 arithmetic, FP64 only in the coefficient precomputation.
+ *
+ * Conventions for every call:
+ *   - Return 0 on success or a negative ADDKER_E* code; addker_strerror() names it.
+ *     No C++ exception crosses this interface.
+ *   - Pointers marked "device" must point to CUDA device memory of the current
+ *     device; "host" pointers to ordinary (or pinned) host memory.
+ *   - The caller owns every buffer it passes in. A plan owns the device buffers
+ *     it allocates (sorted copies of the points, grids, spectra, coefficients)
+ *     and frees them in addker_free().
+ *   - Products are enqueued on the plan's stream (addker_set_stream) and return
+ *     without waiting; the outputs are ready when that stream reaches them.
+ *     Kernel launch failures are reported by the call that launched them, or by
+ *     addker_sync().
+ *   - A plan is not thread-safe: calls on one plan must not overlap in time, and
+ *     two products on one plan must not run concurrently on different streams
+ *     (they share the plan's grids).
+ */
+#ifndef ADDKER_H
+#define ADDKER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define ADDKER_OK        0
+#define ADDKER_EINVAL   -1   /* bad argument (sizes, window layout, bandwidth, cutoff, NULL) */
+#define ADDKER_EDOMAIN  -2   /* a point lies outside the ball ||x^{W_s}|| <= 1/4 - eps_B/2, or is not finite */
+#define ADDKER_ENOMEM   -3   /* a device allocation failed */
+#define ADDKER_ECUDA    -4   /* a CUDA runtime call or kernel launch failed */
+#define ADDKER_ETIMEOUT -5   /* a bounded device wait gave up (reserved) */
+
+/* ---- derivative selectors for addker_dmatvec --------------------------- */
+#define ADDKER_ELL(s)        (s)   /* dK/d ell_s v for window s, 0 <= s < P */
+#define ADDKER_ELL_SHARED   (-1)   /* sum_s dK/d ell_s v: the derivative for one ell shared by all windows */
+#define ADDKER_SIGMA_F      (-2)   /* dK/d sigma_f v = (2/sigma_f) K v */
+
+#define ADDKER_WIN_KB 0            /* Kaiser-Bessel window (the only one implemented) */
+
+typedef struct addker_plan addker_plan;
+
+/* Optional settings; pass NULL to addker_setup for the defaults. */
+typedef struct {
+    double sigma_os;     /* oversampling factor sigma; grid n = sigma * M per dimension (default 2.0) */
+    double eps_B;        /* boundary width eps_B of the regularisation (default 1/16); points must satisfy
+                            ||x^{W_s}|| <= 1/4 - eps_B/2 */
+    int    p;            /* regularisation degree (transition polynomial of degree 2p-1); -1 = default
+                            max(1, round(M eps_B)); 0 = no regularisation (plain periodic continuation) */
+    int    window;       /* ADDKER_WIN_KB */
+    int    reserved;     /* must be 0 */
+    void*  stream;       /* cudaStream_t for every product of this plan; NULL = legacy default stream */
+} addker_opts;
+
+/* Fill *opts with the defaults above. Returns ADDKER_EINVAL for NULL. */
+int addker_opts_default(addker_opts* opts);
+
+/*
+ * Build a plan: validate, sort the points of every window by grid cell, and
+ * precompute the Fourier multipliers (Sec. 3.1 and Sec. 3.3).
+ *
+ *   plan       out: the new plan (NULL on failure)
+ *   points     device, N x d float32, row-major; already scaled so that every
+ *              windowed point satisfies ||x^{W_s}|| <= 1/4 - eps_B/2 (Sec. 3.2);
+ *              copied, the caller may free it after the call
+ *   N, d       number of points (N >= 1) and features (d >= 1)
+ *   win_off    host, P+1 ints, CSR offsets of the windows (win_off[0] = 0)
+ *   win_feat   host, win_off[P] ints: 0-based feature indices of window s are
+ *              win_feat[win_off[s] .. win_off[s+1]); 1 <= d_s <= 3, distinct, < d
+ *   P          number of windows, 1 <= P <= 64
+ *   ell        host, P doubles > 0: length scale of each window, in the units of `points`
+ *   sigma_f    signal standard deviation (> 0)
+ *   bandwidth  host, P ints: M_s, even, 4 <= M_s <= 64 (number of Fourier coefficients per dimension)
+ *   cutoff     window cutoff m, 2 <= m <= 8, with m + 1 <= n/4 + n eps_B/2 for n = sigma M_s
+ *              (so no support wraps around the grid)
+ *   opts       host or NULL
+ *
+ * Errors: ADDKER_EINVAL for bad sizes/layout, ADDKER_EDOMAIN for a point outside
+ * the ball (checked on the device), ADDKER_ENOMEM, ADDKER_ECUDA. Synchronises the
+ * plan's stream before returning.
+ */
+int addker_setup(addker_plan** plan, const float* points, int64_t N, int d,
+                 const int* win_off, const int* win_feat, int P,
+                 const double* ell, double sigma_f, const int* bandwidth, int cutoff,
+                 const addker_opts* opts);
+
+/* Replace the hyperparameters (host ell[P], sigma_f) and recompute the multipliers; the
+ * sorted points are kept. ell may be NULL to keep the length scales. Synchronous. */
+int addker_set_params(addker_plan* plan, const double* ell, double sigma_f);
+
+/* Set the CUDA stream (cudaStream_t, NULL = legacy default) used by later products. */
+int addker_set_stream(addker_plan* plan, void* stream);
+
+/*
+ * Kv = K v. v and Kv: device, N x nrhs float32, column-major (column j is
+ * right-hand side j, leading dimension N). nrhs >= 1.
+ */
+int addker_matvec(addker_plan* plan, const float* v, float* Kv, int nrhs);
+
+/*
+ * out = (dK/d theta) v for theta selected by `param` (ADDKER_ELL(s), ADDKER_ELL_SHARED,
+ * ADDKER_SIGMA_F). v and out: device, N x nrhs float32, column-major.
+ */
+int addker_dmatvec(addker_plan* plan, int param, const float* v, float* out, int nrhs);
+
+/*
+ * The fused product: one spreading per window gives both
+ *   Kv     = K v                      (device, N x nrhs, column-major), and
+ *   dKdell = dK/d ell_s v, s = 0..P-1 (device, N x P x nrhs: column s + P*j holds
+ *            window s of right-hand side j, each column of length N).
+ * dK/d sigma_f v is (2/sigma_f) Kv and is not written. dKdell may be NULL.
+ */
+int addker_matvec_all(addker_plan* plan, const float* v, float* Kv, float* dKdell, int nrhs);
+
+/*
+ * addker_matvec_all with HOST buffers (same layouts): copies v to the device,
+ * runs the fused product on the plan's stream, copies Kv and dKdell back, and
+ * waits for the stream. Pinned host memory makes the copies asynchronous.
+ * Uses plan-owned device staging buffers (allocated on first use).
+ */
+int addker_matvec_all_host(addker_plan* plan, const float* v, float* Kv, float* dKdell, int nrhs);
+
+/* Wait for the plan's stream; report a failed kernel as ADDKER_ECUDA. */
+int addker_sync(addker_plan* plan);
+
+/* Release the plan and every device buffer it owns. NULL is accepted. */
+int addker_free(addker_plan* plan);
+
+/* Human-readable name of a status code (static string). */
+const char* addker_strerror(int status);
+
+/*
+ * Data prescaling of Sec. 3.2 for the given windows: one global factor
+ *   f = (1/4 - eps_B/2) / max_{j,s} ||x_j^{W_s}||
+ * so that every windowed point lands in the ball that addker_setup requires.
+ * X and Xs: device, N x d float32 row-major (Xs may equal X). factor: host, out.
+ * Length scales chosen for X must be multiplied by the same factor. Synchronous
+ * on the given stream (NULL = legacy default).
+ */
+int addker_prescale(const float* X, int64_t N, int d, const int* win_off, const int* win_feat, int P,
+                    double eps_B, float* Xs, double* factor, void* stream);
+
+/*
+ * Plan inspection for tests and benchmarks. Writes up to `cap` int64 values into info:
+ *   [0] N  [1] P  [2] number of work items over all windows  [3] bytes of device memory owned
+ *   then per window s: [4+4s] d_s  [5+4s] M_s  [6+4s] n_s  [7+4s] number of non-empty cells.
+ * Returns the number of values available.
+ */
+int addker_info(const addker_plan* plan, int64_t* info, int cap);
+
+/*
+ * Stage timing for tracing and roofline accounting (not in the paper). While enabled, every
+ * product records CUDA events on the plan's stream around its stages
+ *   0 clearing the grids, 1 spreading, 2 the DFTs with the multiplication, 3 interpolation
+ *   (gather), 4 the sum over windows
+ * and counts the kernels it launches per stage. addker_profile(plan, 1) clears and starts,
+ * addker_profile(plan, 0) stops. addker_profile_read waits for the stream and writes, for
+ * up to `cap` stages, the summed milliseconds ms[i] and kernel launches launches[i]; it returns
+ * the number of stages (5). Either output may be NULL.
+ */
+int addker_profile(addker_plan* plan, int enable);
+int addker_profile_read(addker_plan* plan, double* ms, int64_t* launches, int cap);
+
+/*
+ * Stage-wise check of one window (tests only; synchronous): runs the steps up to `stage`
+ * for right-hand side v (device, N floats) and copies a result to host doubles:
+ *   stage 0: the spread grid g_l, l in I_n^{d_s} (n^{d_s} values, last axis fastest), in the
+ *            normalisation of the window phi(x) = sinh(b sqrt(m^2 - n^2 x^2))/(pi sqrt(m^2 - n^2 x^2));
+ *   stage 1: the adjoint NFFT result S_k ~= sum_j v_j exp(-2 pi i k.x_j), k in I_M^{d_s}
+ *            (2 M^{d_s} values: real, imaginary interleaved, last axis fastest).
+ * `cap` is the capacity of out in doubles. Returns ADDKER_EINVAL if it is too small.
+ */
+int addker_debug_stage(addker_plan* plan, int window, int stage, const float* v, double* out, int64_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADDKER_H */

@@ -148,11 +148,13 @@ def nfft_forward(x: np.ndarray, dhats, n: int, m: int, sigma: float = 2.0) -> np
     return out
 
 
-def nfft_fastsum(x: np.ndarray, v: np.ndarray, chats, n: int, m: int, sigma: float = 2.0) -> np.ndarray:
-    """Level 3: adjoint NFFT -> multiply by c_hat -> NFFT, for each c_hat in chats (rows of the result)."""
+def nfft_fastsum(x: np.ndarray, v: np.ndarray, chats, n: int, m: int, sigma: float = 2.0,
+                 targets: np.ndarray | None = None) -> np.ndarray:
+    """Level 3: adjoint NFFT -> multiply by c_hat -> NFFT, for each c_hat in chats (rows of the result).
+    The sums are evaluated at `targets` (the x'_i of eq. "fast sum"), by default at the sources x."""
     M = chats[0].shape[0]
     S = nfft_adjoint(x, v, M, n, m, sigma)
-    return nfft_forward(x, [c * S for c in chats], n, m, sigma)
+    return nfft_forward(x if targets is None else targets, [c * S for c in chats], n, m, sigma)
 
 
 def window_coefficients(ell: float, d: int, M: int, p: int, eps_B: float):
@@ -161,15 +163,17 @@ def window_coefficients(ell: float, d: int, M: int, p: int, eps_B: float):
 
 
 def matvec_all(points, windows, ell, sigma_f: float, v, bandwidth, cutoff: int, p=None,
-               eps_B: float = 1.0 / 16.0, sigma: float = 2.0, level: str = "nfft"):
-    """Fused product: returns (K v [N], dK/d ell [P, N]) at level 'nfft' (CPU NFFT fast sum)
-    or 'ndft' (exact trigonometric sum). v is one right-hand side of length N."""
+               eps_B: float = 1.0 / 16.0, sigma: float = 2.0, level: str = "nfft", rows=None):
+    """Fused product: returns (K v, dK/d ell [P, .]) at level 'nfft' (CPU NFFT fast sum)
+    or 'ndft' (exact trigonometric sum). v is one right-hand side of length N. With `rows`, the
+    outputs are evaluated only at those points (all N points are still sources)."""
     X = np.asarray(points, dtype=np.float32).astype(np.float64)
     v = np.asarray(v, dtype=np.float64)
-    N = X.shape[0]
     P = len(windows)
     if np.isscalar(bandwidth):
         bandwidth = [int(bandwidth)] * P
+    T = X if rows is None else X[np.asarray(rows)]
+    N = T.shape[0]
     Kv = np.zeros(N)
     dK = np.zeros((P, N))
     for s, w in enumerate(windows):
@@ -178,9 +182,12 @@ def matvec_all(points, windows, ell, sigma_f: float, v, bandwidth, cutoff: int, 
         ps = kernels.default_p(M, eps_B) if p is None else int(p)
         cg, cd = window_coefficients(float(ell[s]), d, M, ps, eps_B)
         xs = np.ascontiguousarray(X[:, list(w)])
+        xt = None if rows is None else np.ascontiguousarray(T[:, list(w)])
         if level == "nfft":
-            outK, outD = nfft_fastsum(xs, v, [cg, cd], int(round(sigma * M)), cutoff, sigma)
+            outK, outD = nfft_fastsum(xs, v, [cg, cd], int(round(sigma * M)), cutoff, sigma, targets=xt)
         elif level == "ndft":
+            if rows is not None:
+                raise ValueError("rows are supported at level 'nfft' only")
             outK, outD = ndft_fastsum(xs, v, [cg, cd])
         else:
             raise ValueError(level)

@@ -1,0 +1,1003 @@
+// C ABI (include/addker.h): plan setup, coefficient precomputation and the product entry points.
+//
+// Setup (not timed with the products):
+//   1. per window, every point's grid cell floor(n x_t) + n/2 and the ball check ||x^W|| <= rho;
+//   2. a counting sort of the points by cell (histogram on the device, offsets and work items on
+//      the host, scatter on the device);
+//   3. the Fourier multipliers, FP64 on the device: samples of the regularised kernel on the
+//      M^D grid j/M, a cosine DFT (Lemma "aliasing error"), division by the window transform;
+//   4. the per-axis twiddles of the pruned DFTs.
+// A product then runs, per right-hand side: clear grids, spread, forward DFT + multiply,
+// inverse DFT, gather (+ window sum), all on the plan's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+#include "common.cuh"
+
+using namespace addker;
+
+struct addker_plan {
+    Plan p;
+};
+
+namespace {
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) {                                  \
+            return e_ == cudaErrorMemoryAllocation ? ADDKER_ENOMEM : ADDKER_ECUDA; \
+        }                                                         \
+    } while (0)
+
+#define CS(status)                        \
+    do {                                  \
+        int s_ = (status);                \
+        if (s_ != ADDKER_OK) return s_;   \
+    } while (0)
+
+template <class T>
+int dalloc(Plan& p, T** ptr, int64_t count)
+{
+    *ptr = nullptr;
+    if (count <= 0) count = 1;
+    void* raw = nullptr;
+    cudaError_t e = cudaMalloc(&raw, sizeof(T) * (size_t)count);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return ADDKER_ENOMEM;
+    }
+    p.allocations.push_back(raw);
+    p.bytes += (int64_t)(sizeof(T) * (size_t)count);
+    *ptr = static_cast<T*>(raw);
+    return ADDKER_OK;
+}
+
+void release(Plan& p)
+{
+    for (void* a : p.allocations) cudaFree(a);
+    p.allocations.clear();
+    p.bytes = 0;
+}
+
+// ------------------------------------------------------------------ setup kernels ----
+
+template <int D>
+__global__ void k_cell_keys(const float* __restrict__ X, int64_t N, int d, int f0, int f1, int f2, int n,
+                            float rho2, int* __restrict__ keys, int* __restrict__ hist, int* __restrict__ bounds,
+                            int* __restrict__ flag)
+{
+    __shared__ int smin[3], smax[3];
+    if (threadIdx.x < 3) { smin[threadIdx.x] = 1 << 30; smax[threadIdx.x] = -(1 << 30); }
+    __syncthreads();
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j < N) {
+        const int f[3] = {f0, f1, f2};
+        float x[3] = {0.f, 0.f, 0.f};
+        float r2 = 0.f;
+        for (int t = 0; t < D; ++t) {
+            x[t] = X[j * d + f[t]];
+            r2 = fmaf(x[t], x[t], r2);
+        }
+        if (!(r2 <= rho2)) {            // also catches NaN
+            atomicOr(flag, 1);
+            keys[j] = -1;
+        } else {
+            int key = 0;
+            for (int t = 0; t < D; ++t) {
+                int c = (int)floorf(x[t] * (float)n) + n / 2;
+                key = key * n + c;
+                atomicMin(&smin[t], c);
+                atomicMax(&smax[t], c);
+            }
+            keys[j] = key;
+            atomicAdd(&hist[key], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < D) {
+        atomicMin(&bounds[threadIdx.x], smin[threadIdx.x]);
+        atomicMax(&bounds[3 + threadIdx.x], smax[threadIdx.x]);
+    }
+}
+
+template <int D>
+__global__ void k_scatter(const float* __restrict__ X, int64_t N, int d, int f0, int f1, int f2,
+                          const int* __restrict__ keys, int* __restrict__ cursor, float4* __restrict__ pts)
+{
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const int f[3] = {f0, f1, f2};
+    float x[3] = {0.f, 0.f, 0.f};
+    for (int t = 0; t < D; ++t) x[t] = X[j * d + f[t]];
+    int pos = atomicAdd(&cursor[keys[j]], 1);
+    pts[pos] = make_float4(x[0], x[1], x[2], __int_as_float((int)j));
+}
+
+// ---------------------------------------------------------- coefficients (FP64) ----
+
+struct Transition {                      // T(r) = sum_i s[i] ((r - a)/h)^i on a < r <= 1/2
+    int np;                              // 2p coefficients (0: no regularisation)
+    double s[2][32];                     // [kind][i], kind 0 Gaussian, 1 derivative kernel
+    double a, h, vb[2];
+};
+
+__device__ double kernel_value(double r, double ell, int kind)
+{
+    double q = r * r / (2.0 * ell * ell);
+    double e = exp(-q);
+    return kind == 0 ? e : q * e;
+}
+
+template <int D>
+__global__ void k_coef_sample(int M, double ell, Transition tr, double* __restrict__ outK, double* __restrict__ outD)
+{
+    int64_t total = 1;
+    for (int t = 0; t < D; ++t) total *= M;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    double r2 = 0.0;
+    int64_t rem = idx;
+    for (int t = 0; t < D; ++t) {
+        int j = (int)(rem % M) - M / 2;
+        rem /= M;
+        double x = (double)j / (double)M;
+        r2 += x * x;
+    }
+    double r = sqrt(r2);
+    for (int kind = 0; kind < 2; ++kind) {
+        double val;
+        if (tr.np == 0 || r <= tr.a) {
+            val = kernel_value(r, ell, kind);
+        } else if (r <= 0.5) {
+            double sg = (r - tr.a) / tr.h, acc = 0.0;
+            for (int i = tr.np - 1; i >= 0; --i) acc = acc * sg + tr.s[kind][i];
+            val = acc;
+        } else {
+            val = tr.vb[kind];
+        }
+        (kind == 0 ? outK : outD)[idx] = val;
+    }
+}
+
+// out[a][k][b] = (1/M) sum_j in[a][j][b] cos(2 pi (j - M/2)(k - M/2) / M); the sine part of the DFT
+// vanishes for even, real samples.
+__global__ void k_coef_dft(const double* __restrict__ in, double* __restrict__ out, int A, int M, int B)
+{
+    int64_t total = (int64_t)A * M * B;
+    int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (o >= total) return;
+    int b = (int)(o % B);
+    int k = (int)((o / B) % M) - M / 2;
+    int a = (int)(o / ((int64_t)B * M));
+    double acc = 0.0;
+    for (int jj = 0; jj < M; ++jj) {
+        int j = jj - M / 2;
+        int ph = ((j * k) % M + M) % M;
+        acc += in[((int64_t)a * M + jj) * B + b] * cospi(2.0 * ph / M);
+    }
+    out[o] = acc / M;
+}
+
+// I_0(z) by its power series sum_i ((z/2)^2)^i / (i!)^2
+__device__ double bessel_i0(double z)
+{
+    double q = 0.25 * z * z, term = 1.0, sum = 1.0;
+    for (int i = 1; i < 400; ++i) {
+        term *= q / ((double)i * (double)i);
+        sum += term;
+        if (term < 1e-18 * sum) break;
+    }
+    return sum;
+}
+
+// Fourier transform of the normalised window w (w(0) = 1) at frequency k on a grid of n:
+//   phi_hat(k) = C I_0(m sqrt(b^2 - (2 pi k/n)^2)) / n,  C = pi m / sinh(b m)
+// (the Kaiser-Bessel pair; exact for the untruncated window, within ~1e-8 of the truncated one).
+__device__ double window_hat(int k, int n, int m, double b)
+{
+    double w = 2.0 * M_PI * k / n;
+    double C = 2.0 * M_PI * m * exp(-b * m) / (1.0 - exp(-2.0 * b * m));
+    return C * bessel_i0(m * sqrt(b * b - w * w)) / n;
+}
+
+template <int D>
+__global__ void k_multipliers(const double* __restrict__ cK, const double* __restrict__ cD, int M, int n, int m,
+                              double b, float* __restrict__ bK, float* __restrict__ bD, float* __restrict__ dconv)
+{
+    int64_t total = 1;
+    for (int t = 0; t < D; ++t) total *= M;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    double ph = 1.0, nd = 1.0;
+    int64_t rem = idx;
+    for (int t = 0; t < D; ++t) {
+        int k = (int)(rem % M) - M / 2;
+        rem /= M;
+        ph *= window_hat(k, n, m, b);
+        nd *= n;
+    }
+    double den = nd * ph;
+    bK[idx] = (float)(cK[idx] / (den * den));
+    bD[idx] = (float)(cD[idx] / (den * den));
+    dconv[idx] = (float)(1.0 / den);
+}
+
+// forward twiddles tf[i][kk] = e^{-2 pi i k l / n}, inverse ti[kk][i] = e^{+2 pi i k l / n},
+// k = kk - M/2, l = lo + i - n/2 (centred index of grid position lo + i)
+__global__ void k_twiddles(float2* __restrict__ tf, float2* __restrict__ ti, int lo, int box, int M, int n)
+{
+    int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= box * M) return;
+    int i = o / M, kk = o % M;
+    int k = kk - M / 2, l = lo + i - n / 2;
+    int ph = (int)((((int64_t)k * l) % n + n) % n);
+    double s, c;
+    sincospi(2.0 * ph / n, &s, &c);
+    tf[i * M + kk] = make_float2((float)c, (float)-s);
+    ti[kk * box + i] = make_float2((float)c, (float)s);
+}
+
+// ---------------------------------------------------------------- products ----
+
+__global__ void k_window_sum(const float* __restrict__ ks, int P, int64_t N, float scale, float* __restrict__ out)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float acc = 0.f;
+    for (int s = 0; s < P; ++s) acc += ks[(int64_t)s * N + i];
+    out[i] = scale * acc;
+}
+
+__global__ void k_max_norm(const float* __restrict__ X, int64_t N, int d, const int* __restrict__ off,
+                           const int* __restrict__ feat, int P, unsigned* __restrict__ result)
+{
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float best = 0.f;
+    if (j < N) {
+        for (int s = 0; s < P; ++s) {
+            float r2 = 0.f;
+            for (int q = off[s]; q < off[s + 1]; ++q) {
+                float x = X[j * d + feat[q]];
+                r2 = fmaf(x, x, r2);
+            }
+            best = fmaxf(best, r2);
+        }
+        if (!(best == best)) best = __int_as_float(0x7f800000);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(result, __float_as_uint(best));
+}
+
+__global__ void k_scale(const float* __restrict__ X, int64_t n, float f, float* __restrict__ Y)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) Y[i] = X[i] * f;
+}
+
+// ------------------------------------------------------------------ host helpers ----
+
+// Taylor coefficients at r = a of the Gaussian (kind 0) or the derivative kernel (kind 1), orders
+// 0..p-1, by power-series arithmetic: exp(-(a+t)^2/c^2) = exp(-a^2/c^2) exp(q(t)),
+// q(t) = -(2 a t + t^2)/c^2, and E = exp(q) satisfies E' = q' E.
+void taylor_at(double a, double ell, int p, int kind, double* out)
+{
+    double c2 = 2.0 * ell * ell;
+    double q1 = -2.0 * a / c2, q2 = -1.0 / c2;
+    std::vector<double> e(p + 2, 0.0);
+    e[0] = 1.0;
+    for (int k = 1; k < p + 2; ++k) e[k] = (q1 * e[k - 1] + (k >= 2 ? 2.0 * q2 * e[k - 2] : 0.0)) / k;
+    double base = std::exp(-a * a / c2);
+    for (int k = 0; k < p + 2; ++k) e[k] *= base;
+    for (int k = 0; k < p; ++k) {
+        if (kind == 0) {
+            out[k] = e[k];
+        } else {                       // ((a + t)^2 / c^2) * series
+            double v = a * a / c2 * e[k];
+            if (k >= 1) v += 2.0 * a / c2 * e[k - 1];
+            if (k >= 2) v += 1.0 / c2 * e[k - 2];
+            out[k] = v;
+        }
+    }
+}
+
+// Transition polynomial of degree 2p-1 on [a, 1/2] (in sigma = (r - a)/h): matches the kernel's
+// first p Taylor coefficients at a, the value kernel(1/2) at 1/2 and p-1 vanishing derivatives there.
+int make_transition(double ell, int p, double eps_B, Transition* tr)
+{
+    std::memset(tr, 0, sizeof(*tr));
+    tr->a = 0.5 - eps_B;
+    tr->h = eps_B;
+    for (int kind = 0; kind < 2; ++kind) {
+        double q = 0.125 / (ell * ell);
+        tr->vb[kind] = kind == 0 ? std::exp(-q) : q * std::exp(-q);
+    }
+    if (p == 0) return ADDKER_OK;
+    if (p > 12) return ADDKER_EINVAL;
+    tr->np = 2 * p;
+    for (int kind = 0; kind < 2; ++kind) {
+        double t[16];
+        taylor_at(tr->a, ell, p, kind, t);
+        double* s = tr->s[kind];
+        for (int i = 0; i < p; ++i) s[i] = t[i] * std::pow(tr->h, i);
+        // equations j = 0..p-1 at sigma = 1: sum_i ff(i, j) s_i = (j == 0 ? vb : 0), ff = falling factorial
+        double A[12][13];
+        for (int j = 0; j < p; ++j) {
+            double rhs = j == 0 ? tr->vb[kind] : 0.0;
+            for (int i = 0; i < 2 * p; ++i) {
+                double ff = 1.0;
+                if (i < j) ff = 0.0;
+                else for (int r = 0; r < j; ++r) ff *= (double)(i - r);
+                if (i < p) rhs -= ff * s[i];
+                else A[j][i - p] = ff;
+            }
+            A[j][p] = rhs;
+        }
+        for (int col = 0; col < p; ++col) {            // Gaussian elimination, partial pivoting
+            int piv = col;
+            for (int r = col + 1; r < p; ++r) if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+            if (A[piv][col] == 0.0) return ADDKER_EINVAL;
+            for (int c = 0; c <= p; ++c) std::swap(A[col][c], A[piv][c]);
+            for (int r = 0; r < p; ++r) {
+                if (r == col) continue;
+                double f = A[r][col] / A[col][col];
+                for (int c = col; c <= p; ++c) A[r][c] -= f * A[col][c];
+            }
+        }
+        for (int j = 0; j < p; ++j) s[p + j] = A[j][p] / A[j][j];
+    }
+    return ADDKER_OK;
+}
+
+int grid_blocks(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+
+int compute_multipliers(Plan& p, int s)
+{
+    WinDev& w = p.win[s];
+    int ps = p.p_opt >= 0 ? p.p_opt : std::max(1, (int)std::lround(w.M * p.eps_B));
+    Transition tr;
+    CS(make_transition(p.ell[s], ps, p.eps_B, &tr));
+    int64_t total = 1;
+    for (int t = 0; t < w.D; ++t) total *= w.M;
+    double *a = nullptr, *b = nullptr, *c = nullptr, *d = nullptr;
+    CK(cudaMalloc(&a, sizeof(double) * total * 4));
+    b = a + total;
+    c = b + total;
+    d = c + total;
+    cudaStream_t st = p.stream;
+    int th = 256, bl = grid_blocks(total, th);
+    if (w.D == 1) k_coef_sample<1><<<bl, th, 0, st>>>(w.M, p.ell[s], tr, a, b);
+    else if (w.D == 2) k_coef_sample<2><<<bl, th, 0, st>>>(w.M, p.ell[s], tr, a, b);
+    else k_coef_sample<3><<<bl, th, 0, st>>>(w.M, p.ell[s], tr, a, b);
+    // separable DFT along each axis (in place via ping-pong): layout [k0]..[k_{D-1}], last fastest
+    double* src[2] = {a, b};
+    double* dst[2] = {c, d};
+    for (int t = 0; t < w.D; ++t) {
+        int64_t B = 1, A = 1;
+        for (int u = t + 1; u < w.D; ++u) B *= w.M;
+        for (int u = 0; u < t; ++u) A *= w.M;
+        for (int q = 0; q < 2; ++q) {
+            k_coef_dft<<<bl, th, 0, st>>>(src[q], dst[q], (int)A, w.M, (int)B);
+            std::swap(src[q], dst[q]);
+        }
+    }
+    double b_shape = M_PI * (2.0 - 1.0 / p.sigma_os);
+    if (w.D == 1) k_multipliers<1><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, w.m, b_shape, (float*)w.bK, (float*)w.bD, (float*)w.dconv);
+    else if (w.D == 2) k_multipliers<2><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, w.m, b_shape, (float*)w.bK, (float*)w.bD, (float*)w.dconv);
+    else k_multipliers<3><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, w.m, b_shape, (float*)w.bK, (float*)w.bD, (float*)w.dconv);
+    cudaError_t e = cudaGetLastError();
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaFree(a);
+    if (e != cudaSuccess || e2 != cudaSuccess) return ADDKER_ECUDA;
+    return ADDKER_OK;
+}
+
+int upload_scales(Plan& p)
+{
+    std::vector<float> sc(3 * p.P);
+    for (int s = 0; s < p.P; ++s) {
+        sc[s] = 1.0f;
+        sc[p.P + s] = (float)(p.sigma_f * p.sigma_f);
+        sc[2 * p.P + s] = (float)(p.sigma_f * p.sigma_f * 2.0 / p.ell[s]);
+    }
+    CK(cudaMemcpy(p.scale_dev, sc.data(), sizeof(float) * sc.size(), cudaMemcpyHostToDevice));
+    return ADDKER_OK;
+}
+
+int setup_window(Plan& p, int s, const float* X, int* keys, int* flag, std::vector<int4>& fast, std::vector<int4>& gen)
+{
+    WinDev& w = p.win[s];
+    const int D = w.D, n = w.n;
+    int f[3] = {0, 0, 0};
+    for (int t = 0; t < D; ++t) f[t] = p.feat[p.feat_off[s] + t];
+    int64_t cells = 1;
+    for (int t = 0; t < D; ++t) cells *= n;
+    int* hist = nullptr;
+    int* bounds = nullptr;
+    CK(cudaMalloc(&hist, sizeof(int) * (cells + 6)));
+    bounds = hist + cells;
+    CK(cudaMemset(hist, 0, sizeof(int) * cells));
+    int binit[6] = {1 << 30, 1 << 30, 1 << 30, -(1 << 30), -(1 << 30), -(1 << 30)};
+    CK(cudaMemcpy(bounds, binit, sizeof(binit), cudaMemcpyHostToDevice));
+    double rho = 0.25 - p.eps_B / 2.0;
+    float rho2 = (float)(rho * rho * (1.0 + 4e-6));
+    int th = 256, bl = grid_blocks(p.N, th);
+    if (D == 1) k_cell_keys<1><<<bl, th>>>(X, p.N, p.d, f[0], f[1], f[2], n, rho2, keys, hist, bounds, flag);
+    else if (D == 2) k_cell_keys<2><<<bl, th>>>(X, p.N, p.d, f[0], f[1], f[2], n, rho2, keys, hist, bounds, flag);
+    else k_cell_keys<3><<<bl, th>>>(X, p.N, p.d, f[0], f[1], f[2], n, rho2, keys, hist, bounds, flag);
+    CK(cudaGetLastError());
+    std::vector<int> h(cells);
+    int bh[6], fl = 0;
+    CK(cudaMemcpy(h.data(), hist, sizeof(int) * cells, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(bh, bounds, sizeof(bh), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&fl, flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (fl) { cudaFree(hist); return ADDKER_EDOMAIN; }
+    // offsets, items (chunks of at most kItemPoints points per cell, heaviest first)
+    std::vector<int> off(cells);
+    int64_t acc = 0;
+    std::vector<int4> items;
+    int ncell = 0;
+    for (int64_t k = 0; k < cells; ++k) {
+        off[k] = (int)acc;
+        int cnt = h[k];
+        if (cnt > 0) {
+            ++ncell;
+            int c[3] = {0, 0, 0};
+            int64_t rem = k;
+            for (int t = D - 1; t >= 0; --t) { c[t] = (int)(rem % n); rem /= n; }
+            int packed = c[0] | (c[1] << 8) | (c[2] << 16);
+            for (int st = 0; st < cnt; st += kItemPoints)
+                items.push_back(make_int4((int)acc + st, std::min(kItemPoints, cnt - st), packed, s));
+        }
+        acc += cnt;
+    }
+    std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) { return a.y > b.y; });
+    p.n_cells[s] = ncell;
+    bool is_fast = (D == 3 && w.m == 4);
+    std::vector<int4>& dst = is_fast ? fast : gen;
+    dst.insert(dst.end(), items.begin(), items.end());
+    // scatter
+    CK(cudaMemcpy(hist, off.data(), sizeof(int) * cells, cudaMemcpyHostToDevice));
+    float4* pts;
+    CS(dalloc(p, &pts, p.N));
+    w.pts = pts;
+    if (D == 1) k_scatter<1><<<bl, th>>>(X, p.N, p.d, f[0], f[1], f[2], keys, hist, pts);
+    else if (D == 2) k_scatter<2><<<bl, th>>>(X, p.N, p.d, f[0], f[1], f[2], keys, hist, pts);
+    else k_scatter<3><<<bl, th>>>(X, p.N, p.d, f[0], f[1], f[2], keys, hist, pts);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    cudaFree(hist);
+    // bounding box of every support: [cmin - m + 1, cmax + m] per axis
+    for (int t = 0; t < 3; ++t) {
+        if (t < D) {
+            w.lo[t] = bh[t] - w.m + 1;
+            w.box[t] = bh[3 + t] + w.m - w.lo[t] + 1;
+            if (w.lo[t] < 0 || w.lo[t] + w.box[t] > n) return ADDKER_EDOMAIN;
+        } else {
+            w.lo[t] = 0;
+            w.box[t] = 1;
+        }
+    }
+    // buffers
+    const int M = w.M;
+    int64_t gsz = (int64_t)w.box[0] * w.box[1] * w.box[2];
+    int64_t md = 1;
+    for (int t = 0; t < D; ++t) md *= M;
+    float* grid;
+    float2* hh;
+    float4 *b1 = nullptr, *b2 = nullptr, *spec;
+    float* mult;
+    CS(dalloc(p, &grid, gsz));
+    CS(dalloc(p, &hh, gsz));
+    if (D == 3) {
+        CS(dalloc(p, &b1, (int64_t)w.box[0] * w.box[1] * M));
+        CS(dalloc(p, &b2, (int64_t)w.box[0] * M * M));
+    } else if (D == 2) {
+        CS(dalloc(p, &b1, (int64_t)w.box[0] * M));
+    }
+    CS(dalloc(p, &spec, md));
+    CS(dalloc(p, &mult, 3 * md));
+    w.grid = grid;
+    w.h = hh;
+    w.buf1 = b1;
+    w.buf2 = b2;
+    w.spec = spec;
+    w.bK = mult;
+    w.bD = mult + md;
+    w.dconv = mult + 2 * md;
+    for (int t = 0; t < 3; ++t) { w.twf[t] = nullptr; w.twi[t] = nullptr; }
+    for (int t = 0; t < D; ++t) {
+        float2* tw;
+        CS(dalloc(p, &tw, 2 * (int64_t)w.box[t] * M));
+        k_twiddles<<<grid_blocks((int64_t)w.box[t] * M, 128), 128>>>(tw, tw + (int64_t)w.box[t] * M, w.lo[t],
+                                                                     w.box[t], M, n);
+        CK(cudaGetLastError());
+        w.twf[t] = tw;
+        w.twi[t] = tw + (int64_t)w.box[t] * M;
+    }
+    return ADDKER_OK;
+}
+
+bool valid_stream_ptrs(const void* ptr)
+{
+    if (!ptr) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// ---- stage profiling --------------------------------------------------------------
+cudaEvent_t take_event(Plan& p)
+{
+    if (!p.ev_pool.empty()) {
+        cudaEvent_t e = p.ev_pool.back();
+        p.ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct Stage {                            // brackets one stage of a product with events when profiling
+    Plan& p;
+    int id;
+    cudaEvent_t a = nullptr;
+    Stage(Plan& plan, int stage) : p(plan), id(stage)
+    {
+        if (p.prof) {
+            a = take_event(p);
+            cudaEventRecord(a, p.stream);
+        }
+    }
+    void done(int launched)
+    {
+        if (!p.prof) return;
+        p.launches[id] += launched;
+        cudaEvent_t b = take_event(p);
+        cudaEventRecord(b, p.stream);
+        p.ev_used.push_back({id, {a, b}});
+    }
+};
+
+// One product for one right-hand side.
+//   mode 0: Kv = K v (if Kv) and dK[s] = dK/d ell_s v for all s (if dK; stride N)
+//   mode 1: dK = dK/d ell_s v for the single window `window`
+//   mode 2: Kv = sum_s dK/d ell_s v (shared length scale)
+int product_one(Plan& p, const float* v, float* Kv, float* dK, int window, int mode)
+{
+    cudaStream_t st = p.stream;
+    const int only = mode == 1 ? window : -1;
+    {
+        Stage sg(p, 0);
+        for (int s = 0; s < p.P; ++s) {
+            if (only >= 0 && s != only) continue;
+            const WinDev& w = p.win[s];
+            CK(cudaMemsetAsync(w.grid, 0, sizeof(float) * (size_t)w.box[0] * w.box[1] * w.box[2], st));
+        }
+        sg.done(0);
+    }
+    {
+        Stage sg(p, 1);
+        int n = 0;
+        CK(launch_spread(p, only, v, st, &n));
+        sg.done(n);
+    }
+    {
+        Stage sg(p, 2);
+        int n = 0;
+        for (int s = 0; s < p.P; ++s) {
+            if (only >= 0 && s != only) continue;
+            CK(launch_fft_forward(p.win[s], st));
+            CK(launch_fft_inverse(p.win[s], st));
+            n += 2 * p.win[s].D;
+        }
+        sg.done(n);
+    }
+    const float* ones = p.scale_dev;
+    const float* sf2 = p.scale_dev + p.P;
+    const float* sder = p.scale_dev + 2 * p.P;
+    int n = 0;
+    Stage sg(p, 3);
+    if (mode == 1) {                               // window s only, written at offset 0
+        CK(launch_gather(p, only, nullptr, 0, dK, 0, ones, sder, st, &n));
+        sg.done(n);
+        return ADDKER_OK;
+    }
+    if (mode == 2) {
+        if (p.P == 1) {
+            CK(launch_gather(p, -1, nullptr, 0, Kv, 0, ones, sder, st, &n));
+            sg.done(n);
+            return ADDKER_OK;
+        }
+        CK(launch_gather(p, -1, nullptr, 0, p.ks, p.N, ones, sder, st, &n));
+        sg.done(n);
+        Stage sum(p, 4);
+        k_window_sum<<<grid_blocks(p.N, 256), 256, 0, st>>>(p.ks, p.P, p.N, 1.0f, Kv);
+        CK(cudaGetLastError());
+        sum.done(1);
+        return ADDKER_OK;
+    }
+    if (p.P == 1) {
+        CK(launch_gather(p, -1, Kv, 0, dK, p.N, sf2, sder, st, &n));
+        sg.done(n);
+        return ADDKER_OK;
+    }
+    CK(launch_gather(p, -1, p.ks, p.N, dK, p.N, ones, sder, st, &n));
+    sg.done(n);
+    Stage sum(p, 4);
+    k_window_sum<<<grid_blocks(p.N, 256), 256, 0, st>>>(p.ks, p.P, p.N, (float)(p.sigma_f * p.sigma_f), Kv);
+    CK(cudaGetLastError());
+    sum.done(1);
+    return ADDKER_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI ====
+
+extern "C" {
+
+const char* addker_strerror(int status)
+{
+    switch (status) {
+        case ADDKER_OK: return "ok";
+        case ADDKER_EINVAL: return "invalid argument";
+        case ADDKER_EDOMAIN: return "point outside the ball ||x^W|| <= 1/4 - eps_B/2 (or not finite)";
+        case ADDKER_ENOMEM: return "device allocation failed";
+        case ADDKER_ECUDA: return "CUDA error";
+        case ADDKER_ETIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+int addker_opts_default(addker_opts* o)
+{
+    if (!o) return ADDKER_EINVAL;
+    o->sigma_os = 2.0;
+    o->eps_B = 1.0 / 16.0;
+    o->p = -1;
+    o->window = ADDKER_WIN_KB;
+    o->reserved = 0;
+    o->stream = nullptr;
+    return ADDKER_OK;
+}
+
+int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const int* win_off, const int* win_feat,
+                 int P, const double* ell, double sigma_f, const int* bandwidth, int cutoff, const addker_opts* opts)
+{
+    if (!out) return ADDKER_EINVAL;
+    *out = nullptr;
+    addker_opts o;
+    addker_opts_default(&o);
+    if (opts) o = *opts;
+    if (N < 1 || N > 0x7fffffffLL || d < 1 || P < 1 || P > kMaxWindows || !win_off || !win_feat || !ell || !bandwidth)
+        return ADDKER_EINVAL;
+    if (!(sigma_f > 0.0) || cutoff < 2 || cutoff > 8 || o.window != ADDKER_WIN_KB || o.reserved != 0) return ADDKER_EINVAL;
+    if (!(o.eps_B > 0.0 && o.eps_B < 0.5) || !(o.sigma_os >= 1.25 && o.sigma_os <= 4.0) || o.p < -1 || o.p > 12)
+        return ADDKER_EINVAL;
+    if (win_off[0] != 0) return ADDKER_EINVAL;
+    for (int s = 0; s < P; ++s) {
+        int ds = win_off[s + 1] - win_off[s];
+        if (ds < 1 || ds > 3 || !(ell[s] > 0.0)) return ADDKER_EINVAL;
+        for (int q = win_off[s]; q < win_off[s + 1]; ++q) {
+            if (win_feat[q] < 0 || win_feat[q] >= d) return ADDKER_EINVAL;
+            for (int r = win_off[s]; r < q; ++r) if (win_feat[r] == win_feat[q]) return ADDKER_EINVAL;
+        }
+        int M = bandwidth[s];
+        if (M < 4 || M > kMaxBandwidth || (M & 1)) return ADDKER_EINVAL;
+        double nd = o.sigma_os * M;
+        int n = (int)std::lround(nd);
+        if (std::fabs(nd - n) > 1e-9 || (n & 1) || n > 128) return ADDKER_EINVAL;
+        if (cutoff + 1 > n / 4.0 + n * o.eps_B / 2.0) return ADDKER_EINVAL;
+    }
+    if (!valid_stream_ptrs(points)) return ADDKER_EINVAL;
+
+    addker_plan* plan = new (std::nothrow) addker_plan;
+    if (!plan) return ADDKER_ENOMEM;
+    Plan& p = plan->p;
+    p.N = N;
+    p.d = d;
+    p.P = P;
+    p.m = cutoff;
+    p.sigma_f = sigma_f;
+    p.sigma_os = o.sigma_os;
+    p.eps_B = o.eps_B;
+    p.p_opt = o.p;
+    p.stream = static_cast<cudaStream_t>(o.stream);
+    p.feat_off.assign(win_off, win_off + P + 1);
+    p.feat.assign(win_feat, win_feat + win_off[P]);
+    p.ell.assign(ell, ell + P);
+    p.bandwidth.assign(bandwidth, bandwidth + P);
+    p.win.resize(P);
+    p.dims.resize(P);
+    p.n_cells.assign(P, 0);
+    double b_shape = M_PI * (2.0 - 1.0 / o.sigma_os);
+    for (int s = 0; s < P; ++s) {
+        WinDev& w = p.win[s];
+        std::memset(&w, 0, sizeof(w));
+        w.D = win_off[s + 1] - win_off[s];
+        p.dims[s] = w.D;
+        w.M = bandwidth[s];
+        w.n = (int)std::lround(o.sigma_os * w.M);
+        w.m = cutoff;
+        w.b = (float)b_shape;
+        w.wnorm = (float)(1.0 / (1.0 - std::exp(-2.0 * b_shape * cutoff)));
+    }
+    int* keys = nullptr;
+    int* flag = nullptr;
+    int status = ADDKER_OK;
+    std::vector<int4> fast, gen;
+    p.item_begin_fast.assign(1, 0);
+    p.item_begin_gen.assign(1, 0);
+    if (cudaMalloc(&keys, sizeof(int) * (size_t)(N + 1)) != cudaSuccess) status = ADDKER_ENOMEM;
+    if (status == ADDKER_OK) {
+        flag = keys + N;
+        if (cudaMemset(flag, 0, sizeof(int)) != cudaSuccess) status = ADDKER_ECUDA;
+    }
+    for (int s = 0; s < P && status == ADDKER_OK; ++s) {
+        status = setup_window(p, s, points, keys, flag, fast, gen);
+        p.item_begin_fast.push_back((int)fast.size());
+        p.item_begin_gen.push_back((int)gen.size());
+    }
+    if (keys) cudaFree(keys);
+    if (status == ADDKER_OK) {
+        status = dalloc(p, &p.items_fast, (int64_t)fast.size());
+        if (status == ADDKER_OK) status = dalloc(p, &p.items_gen, (int64_t)gen.size());
+        if (status == ADDKER_OK && !fast.empty() &&
+            cudaMemcpy(p.items_fast, fast.data(), sizeof(int4) * fast.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            status = ADDKER_ECUDA;
+        if (status == ADDKER_OK && !gen.empty() &&
+            cudaMemcpy(p.items_gen, gen.data(), sizeof(int4) * gen.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            status = ADDKER_ECUDA;
+    }
+    if (status == ADDKER_OK) status = dalloc(p, &p.wins_dev, P);
+    if (status == ADDKER_OK && P > 1) status = dalloc(p, &p.ks, (int64_t)P * N);
+    if (status == ADDKER_OK) status = dalloc(p, &p.scale_dev, 3 * P);
+    for (int s = 0; s < P && status == ADDKER_OK; ++s) status = compute_multipliers(p, s);
+    if (status == ADDKER_OK && cudaMemcpy(p.wins_dev, p.win.data(), sizeof(WinDev) * P, cudaMemcpyHostToDevice) != cudaSuccess)
+        status = ADDKER_ECUDA;
+    if (status == ADDKER_OK) status = upload_scales(p);
+    if (status == ADDKER_OK && cudaDeviceSynchronize() != cudaSuccess) status = ADDKER_ECUDA;
+    if (status != ADDKER_OK) {
+        cudaGetLastError();
+        release(p);
+        delete plan;
+        return status;
+    }
+    *out = plan;
+    return ADDKER_OK;
+}
+
+int addker_set_params(addker_plan* plan, const double* ell, double sigma_f)
+{
+    if (!plan || !(sigma_f > 0.0)) return ADDKER_EINVAL;
+    Plan& p = plan->p;
+    if (ell) {
+        for (int s = 0; s < p.P; ++s) if (!(ell[s] > 0.0)) return ADDKER_EINVAL;
+        p.ell.assign(ell, ell + p.P);
+    }
+    p.sigma_f = sigma_f;
+    CK(cudaStreamSynchronize(p.stream));
+    for (int s = 0; s < p.P; ++s) CS(compute_multipliers(p, s));
+    return upload_scales(p);
+}
+
+int addker_set_stream(addker_plan* plan, void* stream)
+{
+    if (!plan) return ADDKER_EINVAL;
+    plan->p.stream = static_cast<cudaStream_t>(stream);
+    return ADDKER_OK;
+}
+
+int addker_matvec_all(addker_plan* plan, const float* v, float* Kv, float* dKdell, int nrhs)
+{
+    if (!plan || !v || !Kv || nrhs < 1) return ADDKER_EINVAL;
+    Plan& p = plan->p;
+    for (int j = 0; j < nrhs; ++j)
+        CS(product_one(p, v + (int64_t)j * p.N, Kv + (int64_t)j * p.N,
+                       dKdell ? dKdell + (int64_t)j * p.N * p.P : nullptr, -1, 0));
+    return ADDKER_OK;
+}
+
+int addker_matvec(addker_plan* plan, const float* v, float* Kv, int nrhs)
+{
+    return addker_matvec_all(plan, v, Kv, nullptr, nrhs);
+}
+
+int addker_dmatvec(addker_plan* plan, int param, const float* v, float* out, int nrhs)
+{
+    if (!plan || !v || !out || nrhs < 1) return ADDKER_EINVAL;
+    Plan& p = plan->p;
+    if (param >= p.P || param < ADDKER_SIGMA_F) return ADDKER_EINVAL;
+    for (int j = 0; j < nrhs; ++j) {
+        const float* vj = v + (int64_t)j * p.N;
+        float* oj = out + (int64_t)j * p.N;
+        if (param >= 0) {
+            CS(product_one(p, vj, nullptr, oj, param, 1));
+        } else if (param == ADDKER_SIGMA_F) {
+            CS(product_one(p, vj, oj, nullptr, -1, 0));
+            k_scale<<<grid_blocks(p.N, 256), 256, 0, p.stream>>>(oj, p.N, (float)(2.0 / p.sigma_f), oj);
+            CK(cudaGetLastError());
+        } else {
+            CS(product_one(p, vj, oj, nullptr, -1, 2));
+        }
+    }
+    return ADDKER_OK;
+}
+
+int addker_matvec_all_host(addker_plan* plan, const float* v, float* Kv, float* dKdell, int nrhs)
+{
+    if (!plan || !v || !Kv || nrhs < 1) return ADDKER_EINVAL;
+    Plan& p = plan->p;
+    int64_t need = p.N * (int64_t)nrhs;
+    if (need > p.stage_cap) {
+        CS(dalloc(p, &p.stage_v, need));
+        CS(dalloc(p, &p.stage_k, need));
+        CS(dalloc(p, &p.stage_d, need * p.P));
+        p.stage_cap = need;
+    }
+    cudaStream_t st = p.stream;
+    CK(cudaMemcpyAsync(p.stage_v, v, sizeof(float) * need, cudaMemcpyHostToDevice, st));
+    CS(addker_matvec_all(plan, p.stage_v, p.stage_k, dKdell ? p.stage_d : nullptr, nrhs));
+    CK(cudaMemcpyAsync(Kv, p.stage_k, sizeof(float) * need, cudaMemcpyDeviceToHost, st));
+    if (dKdell) CK(cudaMemcpyAsync(dKdell, p.stage_d, sizeof(float) * need * p.P, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return ADDKER_OK;
+}
+
+int addker_sync(addker_plan* plan)
+{
+    if (!plan) return ADDKER_EINVAL;
+    CK(cudaStreamSynchronize(plan->p.stream));
+    CK(cudaGetLastError());
+    return ADDKER_OK;
+}
+
+int addker_profile(addker_plan* plan, int enable)
+{
+    if (!plan) return ADDKER_EINVAL;
+    Plan& p = plan->p;
+    CK(cudaStreamSynchronize(p.stream));
+    for (auto& u : p.ev_used) {
+        p.ev_pool.push_back(u.second.first);
+        p.ev_pool.push_back(u.second.second);
+    }
+    p.ev_used.clear();
+    if (enable) for (int i = 0; i < 5; ++i) p.launches[i] = 0;
+    p.prof = enable != 0;
+    return ADDKER_OK;
+}
+
+int addker_profile_read(addker_plan* plan, double* ms, int64_t* launches, int cap)
+{
+    if (!plan || cap < 0) return ADDKER_EINVAL;
+    Plan& p = plan->p;
+    CK(cudaStreamSynchronize(p.stream));
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (auto& u : p.ev_used) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, u.second.first, u.second.second));
+        acc[u.first] += t;
+    }
+    for (int i = 0; i < cap && i < 5; ++i) {
+        if (ms) ms[i] = acc[i];
+        if (launches) launches[i] = p.launches[i];
+    }
+    return 5;
+}
+
+int addker_free(addker_plan* plan)
+{
+    if (!plan) return ADDKER_OK;
+    cudaStreamSynchronize(plan->p.stream);
+    for (auto& u : plan->p.ev_used) {
+        cudaEventDestroy(u.second.first);
+        cudaEventDestroy(u.second.second);
+    }
+    for (cudaEvent_t e : plan->p.ev_pool) cudaEventDestroy(e);
+    release(plan->p);
+    delete plan;
+    return ADDKER_OK;
+}
+
+int addker_prescale(const float* X, int64_t N, int d, const int* win_off, const int* win_feat, int P, double eps_B,
+                    float* Xs, double* factor, void* stream)
+{
+    if (!X || !Xs || !factor || N < 1 || d < 1 || P < 1 || !win_off || !win_feat || !(eps_B > 0.0 && eps_B < 0.5))
+        return ADDKER_EINVAL;
+    for (int s = 0; s < P; ++s) {
+        if (win_off[s + 1] <= win_off[s]) return ADDKER_EINVAL;
+        for (int q = win_off[s]; q < win_off[s + 1]; ++q) if (win_feat[q] < 0 || win_feat[q] >= d) return ADDKER_EINVAL;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int* buf = nullptr;
+    int nf = win_off[P];
+    CK(cudaMalloc(&buf, sizeof(int) * (P + 1 + nf + 1)));
+    unsigned* res = reinterpret_cast<unsigned*>(buf + P + 1 + nf);
+    cudaMemcpyAsync(buf, win_off, sizeof(int) * (P + 1), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(buf + P + 1, win_feat, sizeof(int) * nf, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(res, 0, sizeof(unsigned), st);
+    k_max_norm<<<grid_blocks(N, 256), 256, 0, st>>>(X, N, d, buf, buf + P + 1, P, res);
+    unsigned bits = 0;
+    cudaMemcpyAsync(&bits, res, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { cudaFree(buf); return ADDKER_ECUDA; }
+    float mx2;
+    std::memcpy(&mx2, &bits, sizeof(float));
+    if (!std::isfinite(mx2)) { cudaFree(buf); return ADDKER_EDOMAIN; }
+    double f = mx2 > 0.f ? (0.25 - eps_B / 2.0) * (1.0 - 4e-7) / std::sqrt((double)mx2) : 1.0;
+    k_scale<<<grid_blocks(N * d, 256), 256, 0, st>>>(X, N * d, (float)f, Xs);
+    e = cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (e != cudaSuccess) return ADDKER_ECUDA;
+    *factor = f;
+    return ADDKER_OK;
+}
+
+int addker_info(const addker_plan* plan, int64_t* info, int cap)
+{
+    if (!plan) return ADDKER_EINVAL;
+    const Plan& p = plan->p;
+    std::vector<int64_t> v = {p.N, p.P, (int64_t)(p.item_begin_fast.back() + p.item_begin_gen.back()), p.bytes};
+    for (int s = 0; s < p.P; ++s) {
+        v.push_back(p.win[s].D);
+        v.push_back(p.win[s].M);
+        v.push_back(p.win[s].n);
+        v.push_back(p.n_cells[s]);
+    }
+    for (int i = 0; i < cap && i < (int)v.size(); ++i) info[i] = v[i];
+    return (int)v.size();
+}
+
+int addker_debug_stage(addker_plan* plan, int window, int stage, const float* v, double* out, int64_t cap)
+{
+    if (!plan || !v || !out) return ADDKER_EINVAL;
+    Plan& p = plan->p;
+    if (window < 0 || window >= p.P || stage < 0 || stage > 1) return ADDKER_EINVAL;
+    WinDev& w = p.win[window];
+    int64_t full = 1, md = 1;
+    for (int t = 0; t < w.D; ++t) { full *= w.n; md *= w.M; }
+    if ((stage == 0 && cap < full) || (stage == 1 && cap < 2 * md)) return ADDKER_EINVAL;
+    cudaStream_t st = p.stream;
+    int64_t gsz = (int64_t)w.box[0] * w.box[1] * w.box[2];
+    CK(cudaMemsetAsync(w.grid, 0, sizeof(float) * gsz, st));
+    CK(launch_spread(p, window, v, st));
+    if (stage == 0) {
+        std::vector<float> g(gsz);
+        CK(cudaMemcpyAsync(g.data(), w.grid, sizeof(float) * gsz, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        // the device window is w = phi * C with C = pi m / sinh(b m); report in phi's normalisation
+        double b = M_PI * (2.0 - 1.0 / p.sigma_os);
+        double C = M_PI * w.m / std::sinh(b * w.m);
+        double scale = std::pow(C, -w.D);
+        std::fill(out, out + full, 0.0);
+        for (int64_t i = 0; i < gsz; ++i) {
+            int64_t i0 = i / ((int64_t)w.box[1] * w.box[2]), i1 = (i / w.box[2]) % w.box[1], i2 = i % w.box[2];
+            int64_t a0 = w.lo[0] + i0, a1 = w.lo[1] + i1, a2 = w.lo[2] + i2;
+            int64_t idx = a0;
+            if (w.D >= 2) idx = idx * w.n + a1;
+            if (w.D >= 3) idx = idx * w.n + a2;
+            out[idx] = g[i] * scale;
+        }
+        return ADDKER_OK;
+    }
+    CK(launch_adjoint_only(w, w.dconv, w.spec, st));
+    std::vector<float4> s(md);
+    CK(cudaMemcpyAsync(s.data(), w.spec, sizeof(float4) * md, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < md; ++i) {
+        out[2 * i] = s[i].x;
+        out[2 * i + 1] = s[i].y;
+    }
+    return ADDKER_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,232 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative L2 over all outputs):
+  - against the oracle's CPU NFFT fast sum with identical settings: 1e-5 (FP32 spreading, DFT and
+    interpolation of sums of up to ~1e6 terms per grid value);
+  - stage-wise: spread grid and adjoint NFFT 1e-5;
+  - against the FP64 direct sum: the method's own Fourier error, measured on the same rows by the
+    oracle's CPU NFFT, plus 1e-5.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import fastsum
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch
+
+
+def make_op(torch, wl, **kw):
+    from paper_2404_17344_gb300 import AddKer
+    return AddKer(torch.from_numpy(wl.points).cuda(), wl.windows, wl.ell, wl.sigma_f, wl.bandwidth, wl.cutoff, **kw)
+
+
+def oracle_all(wl, v, **kw):
+    return fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f, np.asarray(v, np.float64), wl.bandwidth,
+                              wl.cutoff, **kw)
+
+
+@pytest.mark.parametrize("cfg,N", [("c0", 2000), ("c1", 20000), ("c2", 5000)])
+def test_matvec_all_vs_oracle_nfft(torch_cuda, cfg, N):
+    torch = torch_cuda
+    wl = workloads.make(cfg, N=N)
+    v = wl.vector()
+    op = make_op(torch, wl)
+    Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
+    Kr, dKr = oracle_all(wl, v)
+    assert rel(Kv.cpu(), Kr) < TOL
+    for s in range(wl.P):
+        assert rel(dK[s].cpu(), dKr[s]) < TOL, s
+
+
+def test_stage_spread_and_adjoint(torch_cuda):
+    torch = torch_cuda
+    wl = workloads.make("c1", N=30000)
+    v = wl.vector()
+    op = make_op(torch, wl)
+    vd = torch.from_numpy(v).cuda()
+    for s, w in enumerate(wl.windows):
+        x = np.ascontiguousarray(wl.points[:, list(w)].astype(np.float64))
+        g = op.debug_stage(s, 0, vd)
+        gref = np.zeros((64,) * 3)
+        from oracle import _clib, window
+        _clib.lib().orc_spread(len(x), 3, _clib.ptr(x), _clib.ptr(v.astype(np.float64)), 64, 4, window.shape(2.0),
+                               _clib.ptr(gref))
+        assert rel(g, gref) < TOL
+        S = op.debug_stage(s, 1, vd)
+        Sref = fastsum.nfft_adjoint(x, v.astype(np.float64), 32, 64, 4)
+        assert rel(S, Sref) < TOL
+
+
+def test_mixed_window_sizes_and_generic_kernels(torch_cuda):
+    """Windows of 1, 2 and 3 features (generic kernels for d_s < 3) and bandwidths 16/32."""
+    torch = torch_cuda
+    wl = workloads.make("c3", N=20000)
+    v = wl.vector()
+    op = make_op(torch, wl)
+    Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
+    Kr, dKr = oracle_all(wl, v)
+    assert rel(Kv.cpu(), Kr) < TOL
+    for s in range(wl.P):
+        assert rel(dK[s].cpu(), dKr[s]) < TOL, s
+
+
+@pytest.mark.parametrize("m", [2, 3, 5])
+def test_other_cutoffs(torch_cuda, m):
+    torch = torch_cuda
+    wl = workloads.make("c1", N=6000)
+    wl.cutoff = m
+    v = wl.vector()
+    op = make_op(torch, wl)
+    Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
+    Kr, dKr = oracle_all(wl, v)
+    assert rel(Kv.cpu(), Kr) < TOL and rel(dK.cpu(), dKr) < TOL
+
+
+@pytest.mark.parametrize("p", [0, 1, 4])
+def test_regularisation_degrees(torch_cuda, p):
+    torch = torch_cuda
+    wl = workloads.make("c0", N=3000)
+    v = wl.vector()
+    op = make_op(torch, wl, p=p)
+    Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
+    Kr, dKr = oracle_all(wl, v, p=p)
+    assert rel(Kv.cpu(), Kr) < TOL and rel(dK.cpu(), dKr) < TOL
+
+
+def test_dmatvec_selectors_and_multi_rhs(torch_cuda):
+    from paper_2404_17344_gb300 import ADDKER_ELL, ADDKER_ELL_SHARED, ADDKER_SIGMA_F
+    torch = torch_cuda
+    wl = workloads.make("c1", N=10000)
+    wl.sigma_f = 1.7
+    V = torch.from_numpy(wl.vector(nrhs=3)).cuda()
+    op = make_op(torch, wl)
+    Kv, dK = op.matvec_all(V)                    # (N, 3), (P, N, 3)
+    for j in range(3):
+        k1, d1 = op.matvec_all(V[:, j].contiguous())
+        assert rel(Kv[:, j].cpu(), k1.cpu()) < 1e-6
+        assert rel(dK[:, :, j].cpu(), d1.cpu()) < 1e-6
+    Kr, dKr = oracle_all(wl, V[:, 1].cpu().numpy())
+    assert rel(Kv[:, 1].cpu(), Kr) < TOL and rel(dK[:, :, 1].cpu(), dKr) < TOL
+    assert rel(op.matvec(V).cpu(), Kv.cpu()) < 1e-6
+    for s in range(wl.P):
+        assert rel(op.dmatvec(ADDKER_ELL(s), V).cpu(), dK[s].cpu()) < 1e-6
+    assert rel(op.dmatvec(ADDKER_ELL_SHARED, V).cpu(), dK.sum(0).cpu()) < 1e-6
+    assert rel(op.dmatvec(ADDKER_SIGMA_F, V).cpu(), (2.0 / wl.sigma_f) * Kv.cpu()) < 1e-6
+
+
+def test_host_buffers_entry(torch_cuda):
+    torch = torch_cuda
+    wl = workloads.make("c1", N=8000)
+    v = wl.vector()
+    op = make_op(torch, wl)
+    Kd, dKd = op.matvec_all(torch.from_numpy(v).cuda())
+    vh = torch.from_numpy(v).pin_memory()
+    Kh = torch.empty(wl.N).pin_memory()
+    dKh = torch.empty(wl.N * wl.P).pin_memory()
+    op.matvec_all_host(vh, Kh, dKh)
+    assert rel(Kh, Kd.cpu()) < 1e-6 and rel(dKh.reshape(wl.P, wl.N), dKd.cpu()) < 1e-6
+
+
+def test_set_params(torch_cuda):
+    torch = torch_cuda
+    wl = workloads.make("c1", N=6000)
+    v = wl.vector()
+    op = make_op(torch, wl)
+    new_ell = np.array([0.45, 0.2, 0.8])
+    op.set_params(ell=new_ell, sigma_f=0.7)
+    Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
+    wl.ell, wl.sigma_f = new_ell, 0.7
+    Kr, dKr = oracle_all(wl, v)
+    assert rel(Kv.cpu(), Kr) < TOL and rel(dK.cpu(), dKr) < TOL
+
+
+def test_edge_cases(torch_cuda):
+    """N = 1; all points in one cell; a point on the ball's edge; a single 1-D window."""
+    torch = torch_cuda
+    from paper_2404_17344_gb300 import AddKer
+    one = workloads.tiny(N=1, d=3)
+    one.bandwidth, one.cutoff = [32], 4
+    op = make_op(torch, one)
+    Kv, dK = op.matvec_all(torch.ones(1, device="cuda"))
+    Kr, dKr = oracle_all(one, np.ones(1))
+    assert rel(Kv.cpu(), Kr) < TOL and abs(float(dK.cpu()[0, 0])) < 1e-4
+    rng = np.random.default_rng(4)
+    pts = (0.001 + 0.01 / 64 * rng.uniform(0, 1, (700, 3))).astype(np.float32)     # one grid cell
+    pts[0] = [0.21875 * 0.9999, 0.0, 0.0]                                             # and one on the edge
+    wl = workloads.Workload("cell", pts, [(0, 1, 2)], np.array([0.3]), 1.0, [32], 4, 5)
+    v = wl.vector()
+    op = make_op(torch, wl)
+    Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
+    Kr, dKr = oracle_all(wl, v)
+    assert rel(Kv.cpu(), Kr) < TOL and rel(dK.cpu(), dKr) < TOL
+    wl1 = workloads.Workload("1d", pts, [(2,)], np.array([0.2]), 1.0, [64], 4, 5)
+    op = make_op(torch, wl1)
+    Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
+    Kr, dKr = oracle_all(wl1, v)
+    assert rel(Kv.cpu(), Kr) < TOL and rel(dK.cpu(), dKr) < TOL
+
+
+def test_rejects_point_outside_ball(torch_cuda):
+    torch = torch_cuda
+    from paper_2404_17344_gb300 import AddKer, AddkerError
+    pts = np.zeros((100, 3), np.float32)
+    pts[7] = [0.3, 0.0, 0.0]
+    with pytest.raises(AddkerError) as e:
+        AddKer(torch.from_numpy(pts).cuda(), [(0, 1, 2)], [0.5])
+    assert e.value.status == -2
+    pts[7] = [np.nan, 0, 0]
+    with pytest.raises(AddkerError):
+        AddKer(torch.from_numpy(pts).cuda(), [(0, 1, 2)], [0.5])
+
+
+def test_prescale_matches_recipe(torch_cuda):
+    torch = torch_cuda
+    from paper_2404_17344_gb300 import prescale
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((5000, 6)).astype(np.float32)
+    wins = [(0, 1, 2), (3, 4)]
+    Xs, f = prescale(torch.from_numpy(X).cuda(), wins)
+    mx = max(np.sqrt((X[:, list(w)].astype(np.float64) ** 2).sum(1)).max() for w in wins)
+    assert f == pytest.approx((0.25 - 1 / 32) * (1 - 4e-7) / mx, rel=1e-6)
+    np.testing.assert_allclose(Xs.cpu().numpy(), X * np.float32(f), rtol=1e-6)
+
+
+@pytest.mark.slow
+def test_full_size_sampled_rows(torch_cuda):
+    """N = 1e6, d = 9, three windows of 3 (the benchmark workload): GPU outputs on 1500 sampled rows
+    against the CPU NFFT (all 1e6 points spread in FP64) and against the direct FP64 sums."""
+    torch = torch_cuda
+    wl = workloads.make("c1", N=1_000_000)
+    v = wl.vector()
+    op = make_op(torch, wl)
+    Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
+    Kv, dK = Kv.cpu().numpy(), dK.cpu().numpy()
+    rows = np.random.default_rng(0).choice(wl.N, 1500, replace=False)
+    Kn, dKn = oracle_all(wl, v, rows=rows)
+    assert rel(Kv[rows], Kn) < TOL
+    for s in range(wl.P):
+        assert rel(dK[s, rows], dKn[s]) < TOL
+    Kd, dKd = fastsum.direct(wl.points, wl.windows, wl.ell, wl.sigma_f, v.astype(np.float64), rows=rows[:300])
+    method_err = rel(Kn[:300], Kd)
+    assert rel(Kv[rows[:300]], Kd) < method_err + TOL
+    for s in range(wl.P):
+        assert rel(dK[s, rows[:300]], dKd[s]) < rel(dKn[s, :300], dKd[s]) + TOL

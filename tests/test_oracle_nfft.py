@@ -131,3 +131,14 @@ def test_sigma_f_and_derivative_scalings():
         cd = kernels.coefficients(wl.ell[s], 3, 16, kernels.default_p(16, 1 / 16), 1 / 16, "der")
         raw = fastsum.nfft_fastsum(np.ascontiguousarray(X[:, list(w)]), v, [cd], 32, 4)[0]
         np.testing.assert_allclose(D1[s], 2.0 / wl.ell[s] * raw, rtol=1e-13)
+
+
+def test_row_subset_matches_full():
+    """Evaluating the fast sum at a subset of targets gives exactly those rows of the full result."""
+    wl = workloads.make("c1", N=3000)
+    v = wl.vector().astype(np.float64)
+    K, D = fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f, v, wl.bandwidth, wl.cutoff)
+    rows = np.array([5, 0, 2999, 1234])
+    Kr, Dr = fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f, v, wl.bandwidth, wl.cutoff, rows=rows)
+    np.testing.assert_allclose(Kr, K[rows], rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(Dr, D[:, rows], rtol=1e-14, atol=1e-14)
