@@ -100,6 +100,17 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def aggregate(total_ms, e2e_sec, steps, world, dist=None, device="cpu"):
+    """Replicas: every rank ran `steps` products of its own copy of the workload. The job's time is
+    the slowest rank's; value = units of all ranks / that time. Returns (ms_per_step, value, e2e_value)."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([float(total_ms), float(e2e_sec)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, e2e_sec = float(t[0]), float(t[1])
+    return total_ms / steps, world * steps / (total_ms / 1e3), world / e2e_sec
+
+
 def cpu_oracle_step(wl, v, sample_N):
     """One oracle fused product on the first sample_N points (all windows); returns seconds."""
     import oracle
@@ -201,12 +212,6 @@ def run_ours(args, rank, world, local_rank):
     op.profile(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
 
     # end to end through the host-buffer entry point: pinned host v in, Kv and dK out, copies timed
     vh = torch.from_numpy(v_np).pin_memory()
@@ -222,10 +227,7 @@ def run_ours(args, rank, world, local_rank):
         op.matvec_all_host(vh, Kh, dKh)
         e2e_ts.append(time.perf_counter() - t0)
     e2e_sec = sum(e2e_ts) / len(e2e_ts)
-    if dist:
-        t = torch.tensor([e2e_sec], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_sec = float(t.item())
+    ms_per_step, value, e2e_value = aggregate(total_ms, e2e_sec, args.steps, world, dist, dev)
 
     if rank != 0:
         if dist:
@@ -291,7 +293,7 @@ def run_ours(args, rank, world, local_rank):
            "cpu_baseline": {"value": 1.0 / cpu_sec, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                             "sample": f"oracle CPU NFFT fused product on the first {sample} of {N} points, "
                                       f"time scaled by N/sample"},
-           "e2e": {"value": world / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": 4 * N,
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * N,
                    "d2h_bytes_per_step": 4 * N * (1 + P)},
            "gpu_launches": launches * 1,
            "gpu_launches_per_step": launches / args.steps,

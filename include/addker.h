@@ -68,7 +68,7 @@ typedef struct {
     double eps_B;        /* boundary width eps_B of the regularisation (default 1/16); points must satisfy
                             ||x^{W_s}|| <= 1/4 - eps_B/2 */
     int    p;            /* regularisation degree (transition polynomial of degree 2p-1); -1 = default
-                            max(1, round(M eps_B)); 0 = no regularisation (plain periodic continuation) */
+                            max(1, floor(M eps_B + 1/2)); 0 = no regularisation (plain periodic continuation) */
     int    window;       /* ADDKER_WIN_KB */
     int    reserved;     /* must be 0 */
     void*  stream;       /* cudaStream_t for every product of this plan; NULL = legacy default stream */

@@ -102,8 +102,8 @@ def regularised(r, ell: float, p: int, eps_B: float, kind: str = "gauss"):
 
 def default_p(M: int, eps_B: float) -> int:
     """Regularisation degree used when none is given: about the number of coefficient-grid
-    samples that fall in the transition band, round(M eps_B), at least 1."""
-    return max(1, int(round(M * eps_B)))
+    samples that fall in the transition band, M eps_B rounded half up, at least 1."""
+    return max(1, int(np.floor(M * eps_B + 0.5)))
 
 
 def coefficients(ell: float, d: int, M: int, p: int, eps_B: float, kind: str = "gauss"):

@@ -183,31 +183,12 @@ __global__ void k_coef_dft(const double* __restrict__ in, double* __restrict__ o
     out[o] = acc / M;
 }
 
-// I_0(z) by its power series sum_i ((z/2)^2)^i / (i!)^2
-__device__ double bessel_i0(double z)
-{
-    double q = 0.25 * z * z, term = 1.0, sum = 1.0;
-    for (int i = 1; i < 400; ++i) {
-        term *= q / ((double)i * (double)i);
-        sum += term;
-        if (term < 1e-18 * sum) break;
-    }
-    return sum;
-}
-
-// Fourier transform of the normalised window w (w(0) = 1) at frequency k on a grid of n:
-//   phi_hat(k) = C I_0(m sqrt(b^2 - (2 pi k/n)^2)) / n,  C = pi m / sinh(b m)
-// (the Kaiser-Bessel pair; exact for the untruncated window, within ~1e-8 of the truncated one).
-__device__ double window_hat(int k, int n, int m, double b)
-{
-    double w = 2.0 * M_PI * k / n;
-    double C = 2.0 * M_PI * m * exp(-b * m) / (1.0 - exp(-2.0 * b * m));
-    return C * bessel_i0(m * sqrt(b * b - w * w)) / n;
-}
-
+// bK = c_hat / (n^D prod_t phi_hat(k_t))^2, bD likewise, dconv = 1 / (n^D prod_t phi_hat(k_t)),
+// with phat[k + M/2] the Fourier transform of the window the kernels spread with.
 template <int D>
-__global__ void k_multipliers(const double* __restrict__ cK, const double* __restrict__ cD, int M, int n, int m,
-                              double b, float* __restrict__ bK, float* __restrict__ bD, float* __restrict__ dconv)
+__global__ void k_multipliers(const double* __restrict__ cK, const double* __restrict__ cD, int M, int n,
+                              const double* __restrict__ phat, float* __restrict__ bK, float* __restrict__ bD,
+                              float* __restrict__ dconv)
 {
     int64_t total = 1;
     for (int t = 0; t < D; ++t) total *= M;
@@ -216,9 +197,8 @@ __global__ void k_multipliers(const double* __restrict__ cK, const double* __res
     double ph = 1.0, nd = 1.0;
     int64_t rem = idx;
     for (int t = 0; t < D; ++t) {
-        int k = (int)(rem % M) - M / 2;
+        ph *= phat[rem % M];
         rem /= M;
-        ph *= window_hat(k, n, m, b);
         nd *= n;
     }
     double den = nd * ph;
@@ -355,19 +335,115 @@ int make_transition(double ell, int p, double eps_B, Transition* tr)
 
 int grid_blocks(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
 
+// Normalised Kaiser-Bessel window in grid units: w(t) = (m/s) sinh(b s)/sinh(b m), s = sqrt(m^2 - t^2).
+double kb_window(double t, int m, double b)
+{
+    double s2 = (double)m * m - t * t;
+    if (s2 < 0.0) return 0.0;
+    double s = std::sqrt(s2);
+    double bm = b * m;
+    if (s < 1e-7) return m * b * (2.0 * std::exp(-bm)) / (1.0 - std::exp(-2.0 * bm));
+    return (m / s) * (std::exp(b * (s - m)) - std::exp(-b * (s + m))) / (1.0 - std::exp(-2.0 * bm));
+}
+
+// Piece q of the window as a polynomial in u = 2 frac - 1 (t = frac + m - 1 - q): Chebyshev
+// interpolation at kPolyDeg + 1 nodes, converted to monomial coefficients.
+void fit_window_poly(int m, double b, WinPoly* out)
+{
+    std::memset(out, 0, sizeof(*out));
+    const int N = kPolyDeg + 1;
+    for (int q = 0; q < 2 * m; ++q) {
+        double f[kPolyDeg + 1], a[kPolyDeg + 1];
+        for (int j = 0; j < N; ++j) {
+            double x = std::cos(M_PI * (j + 0.5) / N);
+            f[j] = kb_window((x + 1.0) / 2.0 + m - 1 - q, m, b);
+        }
+        for (int k = 0; k < N; ++k) {
+            double acc = 0.0;
+            for (int j = 0; j < N; ++j) acc += f[j] * std::cos(M_PI * k * (j + 0.5) / N);
+            a[k] = 2.0 * acc / N;
+        }
+        a[0] *= 0.5;
+        double Tm[kPolyDeg + 1] = {0}, Tk[kPolyDeg + 1] = {0}, mono[kPolyDeg + 1] = {0};
+        Tm[0] = 1.0;                       // T_0
+        Tk[1] = 1.0;                       // T_1
+        mono[0] += a[0];
+        for (int i = 0; i <= kPolyDeg; ++i) mono[i] += a[1] * Tk[i];
+        for (int k = 2; k < N; ++k) {      // T_k = 2 u T_{k-1} - T_{k-2}
+            double Tn[kPolyDeg + 1] = {0};
+            for (int i = 0; i < kPolyDeg; ++i) Tn[i + 1] += 2.0 * Tk[i];
+            for (int i = 0; i <= kPolyDeg; ++i) Tn[i] -= Tm[i];
+            for (int i = 0; i <= kPolyDeg; ++i) mono[i] += a[k] * Tn[i];
+            std::memcpy(Tm, Tk, sizeof(Tm));
+            std::memcpy(Tk, Tn, sizeof(Tk));
+        }
+        for (int i = 0; i <= kPolyDeg; ++i) out->c[q][i] = (float)mono[i];
+    }
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on P_n from the three-term recurrence).
+void gauss_legendre(int n, double* x, double* w)
+{
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = pk;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// Fourier transform of the window the kernels use (the polynomial pieces, in FP64):
+//   phi_hat(k) = (1/n) int w(t) cos(2 pi k t / n) dt,  piece q covering t in [m-1-q, m-q).
+void window_transform(const WinPoly& poly, int m, int n, int M, double* out)
+{
+    const int nq = 24;
+    double gx[nq], gw[nq];
+    gauss_legendre(nq, gx, gw);
+    for (int kk = 0; kk < M; ++kk) {
+        const int k = kk - M / 2;
+        double acc = 0.0;
+        for (int q = 0; q < 2 * m; ++q) {
+            for (int i = 0; i < nq; ++i) {
+                double u = gx[i];                            // u in [-1, 1], frac = (u + 1)/2
+                double t = (u + 1.0) / 2.0 + m - 1 - q;
+                double val = 0.0;
+                for (int c = kPolyDeg; c >= 0; --c) val = val * u + (double)poly.c[q][c];
+                acc += 0.5 * gw[i] * val * std::cos(2.0 * M_PI * k * t / n);
+            }
+        }
+        out[kk] = acc / n;
+    }
+}
+
 int compute_multipliers(Plan& p, int s)
 {
     WinDev& w = p.win[s];
-    int ps = p.p_opt >= 0 ? p.p_opt : std::max(1, (int)std::lround(w.M * p.eps_B));
+    // default degree: M eps_B rounded half up, at least 1
+    int ps = p.p_opt >= 0 ? p.p_opt : std::max(1, (int)std::floor(w.M * p.eps_B + 0.5));
     Transition tr;
     CS(make_transition(p.ell[s], ps, p.eps_B, &tr));
     int64_t total = 1;
     for (int t = 0; t < w.D; ++t) total *= w.M;
-    double *a = nullptr, *b = nullptr, *c = nullptr, *d = nullptr;
-    CK(cudaMalloc(&a, sizeof(double) * total * 4));
+    double *a = nullptr, *b = nullptr, *c = nullptr, *d = nullptr, *ph = nullptr;
+    CK(cudaMalloc(&a, sizeof(double) * (total * 4 + w.M)));
     b = a + total;
     c = b + total;
     d = c + total;
+    ph = d + total;
+    std::vector<double> phat(w.M);
+    window_transform(p.poly, w.m, w.n, w.M, phat.data());
+    CK(cudaMemcpy(ph, phat.data(), sizeof(double) * w.M, cudaMemcpyHostToDevice));
     cudaStream_t st = p.stream;
     int th = 256, bl = grid_blocks(total, th);
     if (w.D == 1) k_coef_sample<1><<<bl, th, 0, st>>>(w.M, p.ell[s], tr, a, b);
@@ -385,10 +461,9 @@ int compute_multipliers(Plan& p, int s)
             std::swap(src[q], dst[q]);
         }
     }
-    double b_shape = M_PI * (2.0 - 1.0 / p.sigma_os);
-    if (w.D == 1) k_multipliers<1><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, w.m, b_shape, (float*)w.bK, (float*)w.bD, (float*)w.dconv);
-    else if (w.D == 2) k_multipliers<2><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, w.m, b_shape, (float*)w.bK, (float*)w.bD, (float*)w.dconv);
-    else k_multipliers<3><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, w.m, b_shape, (float*)w.bK, (float*)w.bD, (float*)w.dconv);
+    if (w.D == 1) k_multipliers<1><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, (float*)w.bK, (float*)w.bD, (float*)w.dconv);
+    else if (w.D == 2) k_multipliers<2><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, (float*)w.bK, (float*)w.bD, (float*)w.dconv);
+    else k_multipliers<3><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, (float*)w.bK, (float*)w.bD, (float*)w.dconv);
     cudaError_t e = cudaGetLastError();
     cudaError_t e2 = cudaStreamSynchronize(st);
     cudaFree(a);
@@ -494,7 +569,7 @@ int setup_window(Plan& p, int s, const float* X, int* keys, int* flag, std::vect
     CS(dalloc(p, &grid, gsz));
     CS(dalloc(p, &hh, gsz));
     if (D == 3) {
-        CS(dalloc(p, &b1, (int64_t)w.box[0] * w.box[1] * M));
+        CS(dalloc(p, &b1, (int64_t)w.box[0] * std::max(w.box[1], M) * M));
         CS(dalloc(p, &b2, (int64_t)w.box[0] * M * M));
     } else if (D == 2) {
         CS(dalloc(p, &b1, (int64_t)w.box[0] * M));
@@ -593,12 +668,7 @@ int product_one(Plan& p, const float* v, float* Kv, float* dK, int window, int m
     {
         Stage sg(p, 2);
         int n = 0;
-        for (int s = 0; s < p.P; ++s) {
-            if (only >= 0 && s != only) continue;
-            CK(launch_fft_forward(p.win[s], st));
-            CK(launch_fft_inverse(p.win[s], st));
-            n += 2 * p.win[s].D;
-        }
+        CK(launch_transforms(p, only, st, &n, false));
         sg.done(n);
     }
     const float* ones = p.scale_dev;
@@ -729,8 +799,8 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
         w.n = (int)std::lround(o.sigma_os * w.M);
         w.m = cutoff;
         w.b = (float)b_shape;
-        w.wnorm = (float)(1.0 / (1.0 - std::exp(-2.0 * b_shape * cutoff)));
     }
+    fit_window_poly(cutoff, b_shape, &p.poly);
     int* keys = nullptr;
     int* flag = nullptr;
     int status = ADDKER_OK;
@@ -989,7 +1059,7 @@ int addker_debug_stage(addker_plan* plan, int window, int stage, const float* v,
         }
         return ADDKER_OK;
     }
-    CK(launch_adjoint_only(w, w.dconv, w.spec, st));
+    CK(launch_transforms(p, window, st, nullptr, true));
     std::vector<float4> s(md);
     CK(cudaMemcpyAsync(s.data(), w.spec, sizeof(float4) * md, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

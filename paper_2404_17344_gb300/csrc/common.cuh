@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "../../include/addker.h"
@@ -25,6 +26,17 @@ namespace addker {
 constexpr int kMaxWindows = 64;
 constexpr int kItemPoints = 256;        // points per work item (one warp)
 constexpr int kMaxBandwidth = 64;
+
+// Piecewise polynomial form of the window used by every spreading/interpolation kernel: for a
+// coordinate with fractional grid offset frac = n x - floor(n x) in [0, 1), the weight of support
+// index q (grid index floor(n x) - m + 1 + q) is  w_q = sum_i c[q][i] u^i,  u = 2 frac - 1.
+// Fitted at setup (FP64 Chebyshev interpolation of the normalised Kaiser-Bessel window) to about
+// 1e-7 of the peak; passed by value, so the coefficients sit in the constant bank.
+constexpr int kPolyDeg = 9;
+constexpr int kMaxW = 16;
+struct WinPoly {
+    float c[kMaxW][kPolyDeg + 1];
+};
 
 struct WinDev {                          // copied by value into kernel parameter space
     const float4* pts;
@@ -42,7 +54,6 @@ struct WinDev {                          // copied by value into kernel paramete
     int lo[3];                           // grid-array index (l + n/2) of the box origin per axis
     int box[3];
     float b;                             // Kaiser-Bessel shape pi (2 - 1/sigma)
-    float wnorm;                         // 1 / (1 - exp(-2 b m))
 };
 
 struct Plan {
@@ -61,6 +72,7 @@ struct Plan {
     int4* items_fast = nullptr;
     int4* items_gen = nullptr;
     std::vector<int> item_begin_fast, item_begin_gen;
+    WinPoly poly;                         // window polynomials for cutoff m and shape b
     float* scale_dev = nullptr;           // 3P floats: [0,P) ones, [P,2P) sigma_f^2, [2P,3P) sigma_f^2 2/ell_s
     float* ks = nullptr;                  // P x N per-window K_s v, scratch for the window sum
     float* stage_v = nullptr;             // host-API staging (N x nrhs), allocated on demand
@@ -76,21 +88,37 @@ struct Plan {
     int64_t launches[5] = {0, 0, 0, 0, 0};
 };
 
-// ---- device window function --------------------------------------------------------
-// Kaiser-Bessel window in grid units t = n x - l, normalised to 1 at t = 0:
-//   w(t) = (m / s) sinh(b s) / sinh(b m),   s = sqrt(m^2 - t^2),   |t| <= m.
-// Written as (m/s) (e^{b(s-m)} - e^{-b(s+m)}) / (1 - e^{-2bm}) so no term overflows; for tiny s
-// the series sinh(bs)/s = b (1 + (bs)^2/6) is used.
-__device__ __forceinline__ float kb_weight(float t, float b, float m, float wnorm)
+// ---- device window weights ------------------------------------------------------------
+// The W = 2m weights of one coordinate x on a grid of n points; *cell = floor(n x) + n/2.
+template <int W>
+__device__ __forceinline__ void window_weights(const WinPoly& P, float x, int n, float* w, int* cell)
 {
-    float s2 = fmaxf(m * m - t * t, 0.0f);
-    float s = sqrtf(s2);
-    if (s > 1e-3f) {
-        float e1 = expf(b * (s - m));
-        float e2 = expf(-b * (s + m));
-        return (m / s) * (e1 - e2) * wnorm;
+    const float u = x * (float)n;
+    const float fl = floorf(u);
+    const float t = 2.0f * (u - fl) - 1.0f;
+    *cell = (int)fl + n / 2;
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        float acc = P.c[q][kPolyDeg];
+#pragma unroll
+        for (int i = kPolyDeg - 1; i >= 0; --i) acc = fmaf(acc, t, P.c[q][i]);
+        w[q] = acc;
     }
-    return m * b * (1.0f + b * b * s2 * (1.0f / 6.0f)) * 2.0f * expf(-b * m) * wnorm;
+}
+
+// runtime W (generic kernels)
+__device__ __forceinline__ void window_weights_n(const WinPoly& P, float x, int n, int W, float* w, int* cell)
+{
+    const float u = x * (float)n;
+    const float fl = floorf(u);
+    const float t = 2.0f * (u - fl) - 1.0f;
+    *cell = (int)fl + n / 2;
+    for (int q = 0; q < W; ++q) {
+        float acc = P.c[q][kPolyDeg];
+#pragma unroll
+        for (int i = kPolyDeg - 1; i >= 0; --i) acc = fmaf(acc, t, P.c[q][i]);
+        w[q] = acc;
+    }
 }
 
 // ---- launchers implemented in the other translation units -------------------------
@@ -101,9 +129,8 @@ cudaError_t launch_spread(const Plan& p, int window_or_all, const float* v, cuda
 cudaError_t launch_gather(const Plan& p, int window_or_all, float* outK, int64_t strideK, float* outD,
                           int64_t strideD, const float* scaleK, const float* scaleD, cudaStream_t st,
                           int* count = nullptr);
-cudaError_t launch_fft_forward(const WinDev& w, cudaStream_t st);   // grid -> spec (two spectra), D launches
-cudaError_t launch_fft_inverse(const WinDev& w, cudaStream_t st);   // spec -> h, D launches
-cudaError_t launch_adjoint_only(const WinDev& w, const float* dconv, float4* out,
-                                cudaStream_t st);                    // grid -> S_k (adjoint NFFT)
+// grid -> (multiply) -> h for one window or all (window < 0). spec_only: stop after the forward
+// transform and write S_k = G_k dconv_k (the adjoint NFFT) to each window's spec.
+cudaError_t launch_transforms(const Plan& p, int window_or_all, cudaStream_t st, int* count, bool spec_only);
 
 }  // namespace addker
