@@ -245,11 +245,15 @@ def run_ours(args, rank, world, local_rank):
     dom_ms, dom_launches = stage[dom]
     per_launch_s = dom_ms / 1e3 / max(1, dom_launches)
     achieved = flops[dom] / per_launch_s / 1e12
-    traffic = None
+    traffic = None                       # from the last ncu capture, only while the kernel source is unchanged
     tfile = os.path.join(ROOT, "profiles", f"{dom}_traffic.json")
     if os.path.exists(tfile):
         try:
-            traffic = json.load(open(tfile)).get("bytes_per_launch")
+            import hashlib
+            rec = json.load(open(tfile))
+            src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+            if hashlib.sha256(src).hexdigest() == rec["source_sha256"]:
+                traffic = rec["bytes_per_launch"]
         except Exception:
             traffic = None
     # algorithmic HBM bytes per unit: coordinates read twice (36 B each), v (4 B), outputs 4(1+P) B per point

@@ -347,12 +347,13 @@ double kb_window(double t, int m, double b)
 }
 
 // Piece q of the window as a polynomial in u = 2 frac - 1 (t = frac + m - 1 - q): Chebyshev
-// interpolation at kPolyDeg + 1 nodes, converted to monomial coefficients.
+// interpolation at kPolyDeg + 1 nodes, converted to monomial coefficients, stored as its even part
+// (coefficients of u^0, u^2, ...) and odd part (u^1, u^3, ...); pieces q >= m are the mirror images.
 void fit_window_poly(int m, double b, WinPoly* out)
 {
     std::memset(out, 0, sizeof(*out));
     const int N = kPolyDeg + 1;
-    for (int q = 0; q < 2 * m; ++q) {
+    for (int q = 0; q < m; ++q) {
         double f[kPolyDeg + 1], a[kPolyDeg + 1];
         for (int j = 0; j < N; ++j) {
             double x = std::cos(M_PI * (j + 0.5) / N);
@@ -377,8 +378,24 @@ void fit_window_poly(int m, double b, WinPoly* out)
             std::memcpy(Tm, Tk, sizeof(Tm));
             std::memcpy(Tk, Tn, sizeof(Tk));
         }
-        for (int i = 0; i <= kPolyDeg; ++i) out->c[q][i] = (float)mono[i];
+        for (int i = 0; i <= kPolyDeg; ++i) {
+            if (i % 2 == 0) out->e[q][i / 2] = (float)mono[i];
+            else out->o[q][i / 2] = (float)mono[i];
+        }
     }
+}
+
+// Value of window piece q at u, from the stored even/odd parts (the device evaluates the same form).
+double window_piece(const WinPoly& poly, int m, int q, double u)
+{
+    const bool mirror = q >= m;
+    const int qq = mirror ? 2 * m - 1 - q : q;
+    double E = 0.0, O = 0.0, u2 = u * u;
+    for (int i = kHalfCoef - 1; i >= 0; --i) {
+        E = E * u2 + (double)poly.e[qq][i];
+        O = O * u2 + (double)poly.o[qq][i];
+    }
+    return mirror ? E - u * O : E + u * O;
 }
 
 // Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on P_n from the three-term recurrence).
@@ -417,9 +434,7 @@ void window_transform(const WinPoly& poly, int m, int n, int M, double* out)
             for (int i = 0; i < nq; ++i) {
                 double u = gx[i];                            // u in [-1, 1], frac = (u + 1)/2
                 double t = (u + 1.0) / 2.0 + m - 1 - q;
-                double val = 0.0;
-                for (int c = kPolyDeg; c >= 0; --c) val = val * u + (double)poly.c[q][c];
-                acc += 0.5 * gw[i] * val * std::cos(2.0 * M_PI * k * t / n);
+                acc += 0.5 * gw[i] * window_piece(poly, m, q, u) * std::cos(2.0 * M_PI * k * t / n);
             }
         }
         out[kk] = acc / n;

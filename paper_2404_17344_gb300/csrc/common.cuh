@@ -28,14 +28,19 @@ constexpr int kItemPoints = 256;        // points per work item (one warp)
 constexpr int kMaxBandwidth = 64;
 
 // Piecewise polynomial form of the window used by every spreading/interpolation kernel: for a
-// coordinate with fractional grid offset frac = n x - floor(n x) in [0, 1), the weight of support
-// index q (grid index floor(n x) - m + 1 + q) is  w_q = sum_i c[q][i] u^i,  u = 2 frac - 1.
+// coordinate with fractional grid offset frac = n x - floor(n x) in [0, 1) and u = 2 frac - 1, the
+// weight of support index q (grid index floor(n x) - m + 1 + q) is a polynomial P_q(u) of degree
+// kPolyDeg. The window is even, so piece W-1-q is piece q mirrored, P_{W-1-q}(u) = P_q(-u); with
+// P_q(u) = E_q(u^2) + u O_q(u^2) both come from one even and one odd part:
+//   w_q = E_q(u^2) + u O_q(u^2),   w_{W-1-q} = E_q(u^2) - u O_q(u^2),   q < m.
 // Fitted at setup (FP64 Chebyshev interpolation of the normalised Kaiser-Bessel window) to about
 // 1e-7 of the peak; passed by value, so the coefficients sit in the constant bank.
 constexpr int kPolyDeg = 9;
 constexpr int kMaxW = 16;
+constexpr int kHalfCoef = (kPolyDeg + 2) / 2;    // coefficients of E_q and O_q each
 struct WinPoly {
-    float c[kMaxW][kPolyDeg + 1];
+    float e[kMaxW / 2][kHalfCoef];
+    float o[kMaxW / 2][kHalfCoef];
 };
 
 struct WinDev {                          // copied by value into kernel parameter space
@@ -90,35 +95,39 @@ struct Plan {
 
 // ---- device window weights ------------------------------------------------------------
 // The W = 2m weights of one coordinate x on a grid of n points; *cell = floor(n x) + n/2.
+__device__ __forceinline__ void window_pair(const WinPoly& P, int q, float u, float u2, float* lo, float* hi)
+{
+    float E = P.e[q][kHalfCoef - 1], O = P.o[q][kHalfCoef - 1];
+#pragma unroll
+    for (int i = kHalfCoef - 2; i >= 0; --i) {
+        E = fmaf(E, u2, P.e[q][i]);
+        O = fmaf(O, u2, P.o[q][i]);
+    }
+    *lo = fmaf(u, O, E);
+    *hi = fmaf(-u, O, E);
+}
+
 template <int W>
 __device__ __forceinline__ void window_weights(const WinPoly& P, float x, int n, float* w, int* cell)
 {
-    const float u = x * (float)n;
-    const float fl = floorf(u);
-    const float t = 2.0f * (u - fl) - 1.0f;
+    const float s = x * (float)n;
+    const float fl = floorf(s);
+    const float u = 2.0f * (s - fl) - 1.0f;
+    const float u2 = u * u;
     *cell = (int)fl + n / 2;
 #pragma unroll
-    for (int q = 0; q < W; ++q) {
-        float acc = P.c[q][kPolyDeg];
-#pragma unroll
-        for (int i = kPolyDeg - 1; i >= 0; --i) acc = fmaf(acc, t, P.c[q][i]);
-        w[q] = acc;
-    }
+    for (int q = 0; q < W / 2; ++q) window_pair(P, q, u, u2, &w[q], &w[W - 1 - q]);
 }
 
 // runtime W (generic kernels)
 __device__ __forceinline__ void window_weights_n(const WinPoly& P, float x, int n, int W, float* w, int* cell)
 {
-    const float u = x * (float)n;
-    const float fl = floorf(u);
-    const float t = 2.0f * (u - fl) - 1.0f;
+    const float s = x * (float)n;
+    const float fl = floorf(s);
+    const float u = 2.0f * (s - fl) - 1.0f;
+    const float u2 = u * u;
     *cell = (int)fl + n / 2;
-    for (int q = 0; q < W; ++q) {
-        float acc = P.c[q][kPolyDeg];
-#pragma unroll
-        for (int i = kPolyDeg - 1; i >= 0; --i) acc = fmaf(acc, t, P.c[q][i]);
-        w[q] = acc;
-    }
+    for (int q = 0; q < W / 2; ++q) window_pair(P, q, u, u2, &w[q], &w[W - 1 - q]);
 }
 
 // ---- launchers implemented in the other translation units -------------------------

@@ -10,11 +10,11 @@
 // (2m)^D grid points. The fast kernels (D = 3, m = 4) exploit that:
 //   spread: a warp accumulates the item's 8x8x8 box in registers as a sum of outer products
 //           (v_j w_x) (x) w_y (x) w_z; lane (ah, bh, c) owns the 4x4 block a in 4ah..4ah+3,
-//           b in 4bh..4bh+3 at z-offset c, so each point costs a lane 3 shared loads, 4 products
-//           and 16 FMAs; the box is added to the grid once per item;
+//           b in 4bh..4bh+3 at z-offset c, so each point costs a lane 4 shared loads, 2 packed
+//           products and 8 packed FMAs; the box is added to the grid once per item;
 //   gather: a warp stages the item's box of both grids in shared memory (float2 (h^K, h^der)) and
-//           every lane contracts it with two points at once, so one 16-byte broadcast load feeds
-//           8 FMAs.
+//           every lane contracts it with two points at once, the grid pair in one packed FMA, so
+//           one 16-byte broadcast load feeds 8 FMAs in 4 instructions.
 #include "common.cuh"
 
 namespace addker {
@@ -24,13 +24,19 @@ namespace {
 constexpr int kWarps = 8;                 // warps per block in the item kernels
 
 // ----------------------------------------------------------------------------------
+// Packed FP32 pairs (one instruction, two FMAs): the fast kernels keep their accumulators in
+// float2 pairs and use __ffma2_rn.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
 // fast 3-D spread, m = 4 (W = 8)
+// Staged per point (STRIDE floats): xp[8] pairs (x_a v, x_a v) | wy[8] | zp[8] pairs (z_c, z_c).
+// Lane (ah, bh, c) accumulates acc[a][p] = (g[4ah+a][4bh+2p][c], g[4ah+a][4bh+2p+1][c]).
 __global__ void __launch_bounds__(kWarps * 32) k_spread3_w8(const int4* __restrict__ items, int nitems,
                                                            const WinDev* __restrict__ wins,
                                                            const float* __restrict__ v, const WinPoly poly)
 {
     constexpr int W = 8;
-    constexpr int STRIDE = 28;            // floats per staged point: wx*v[8] wy[8] wz[8] pad[4]
+    constexpr int STRIDE = 44;            // 16 + 8 + 16 floats, padded so staging stores avoid conflicts
     __shared__ __align__(16) float sw[kWarps][32 * STRIDE];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int item = blockIdx.x * kWarps + warp;
@@ -43,19 +49,26 @@ __global__ void __launch_bounds__(kWarps * 32) k_spread3_w8(const int4* __restri
     float* ws = sw[warp];
     const int ah = lane >> 4, bh = (lane >> 3) & 1, c = lane & 7;
 
-    float acc[4][4];
+    float2 acc[4][2];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int a = 0; a < 4; ++a) { acc[a][0] = f2(0.f, 0.f); acc[a][1] = f2(0.f, 0.f); }
 
+    // software pipeline: the next batch's point (and then its v) is in flight during this batch
+    float4 pn = make_float4(0.f, 0.f, 0.f, 0.f);
+    float vn = 0.f;
+    if (lane < count) {
+        pn = pts[lane];
+        vn = __ldg(v + __float_as_int(pn.w));
+    }
     for (int base = 0; base < count; base += 32) {
-        const int k = base + lane;
+        const float4 p = pn;
+        const float vv = vn;
+        const bool valid = base + lane < count;
+        const int kn = base + 32 + lane;
+        if (kn < count) pn = pts[kn];
         float wx[W], wy[W], wz[W];
         int cx, cy, cz;
-        if (k < count) {
-            const float4 p = pts[k];
-            const float vv = __ldg(v + __float_as_int(p.w));
+        if (valid) {
             window_weights<W>(poly, p.x, n, wx, &cx);
             window_weights<W>(poly, p.y, n, wy, &cy);
             window_weights<W>(poly, p.z, n, wz, &cz);
@@ -65,27 +78,31 @@ __global__ void __launch_bounds__(kWarps * 32) k_spread3_w8(const int4* __restri
 #pragma unroll
             for (int q = 0; q < W; ++q) { wx[q] = 0.f; wy[q] = 0.f; wz[q] = 0.f; }
         }
+        if (kn < count) vn = __ldg(v + __float_as_int(pn.w));
         float4* dst = reinterpret_cast<float4*>(ws + lane * STRIDE);
-        dst[0] = make_float4(wx[0], wx[1], wx[2], wx[3]);
-        dst[1] = make_float4(wx[4], wx[5], wx[6], wx[7]);
-        dst[2] = make_float4(wy[0], wy[1], wy[2], wy[3]);
-        dst[3] = make_float4(wy[4], wy[5], wy[6], wy[7]);
-        dst[4] = make_float4(wz[0], wz[1], wz[2], wz[3]);
-        dst[5] = make_float4(wz[4], wz[5], wz[6], wz[7]);
+#pragma unroll
+        for (int q = 0; q < W; q += 2) dst[q / 2] = make_float4(wx[q], wx[q], wx[q + 1], wx[q + 1]);
+        dst[4] = make_float4(wy[0], wy[1], wy[2], wy[3]);
+        dst[5] = make_float4(wy[4], wy[5], wy[6], wy[7]);
+#pragma unroll
+        for (int q = 0; q < W; q += 2) dst[6 + q / 2] = make_float4(wz[q], wz[q], wz[q + 1], wz[q + 1]);
         __syncwarp();
         const int cnt = min(32, count - base);
         const float* src = ws;
 #pragma unroll 4
         for (int j = 0; j < cnt; ++j, src += STRIDE) {
-            const float4 xa = *reinterpret_cast<const float4*>(src + 4 * ah);
-            const float4 yb = *reinterpret_cast<const float4*>(src + 8 + 4 * bh);
-            const float zc = src[16 + c];
-            const float B[4] = {yb.x * zc, yb.y * zc, yb.z * zc, yb.w * zc};
-            const float X[4] = {xa.x, xa.y, xa.z, xa.w};
+            const float4 x01 = *reinterpret_cast<const float4*>(src + 8 * ah);        // a = 4ah, 4ah+1
+            const float4 x23 = *reinterpret_cast<const float4*>(src + 8 * ah + 4);    // a = 4ah+2, 4ah+3
+            const float4 yb = *reinterpret_cast<const float4*>(src + 16 + 4 * bh);
+            const float2 zz = *reinterpret_cast<const float2*>(src + 24 + 2 * c);
+            const float2 B01 = __fmul2_rn(f2(yb.x, yb.y), zz);
+            const float2 B23 = __fmul2_rn(f2(yb.z, yb.w), zz);
+            const float2 X[4] = {f2(x01.x, x01.y), f2(x01.z, x01.w), f2(x23.x, x23.y), f2(x23.z, x23.w)};
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(X[a], B[b], acc[a][b]);
+            for (int a = 0; a < 4; ++a) {
+                acc[a][0] = __ffma2_rn(X[a], B01, acc[a][0]);
+                acc[a][1] = __ffma2_rn(X[a], B23, acc[a][1]);
+            }
         }
         __syncwarp();
     }
@@ -95,14 +112,93 @@ __global__ void __launch_bounds__(kWarps * 32) k_spread3_w8(const int4* __restri
     const int sy = P.box[2], sx = P.box[1] * P.box[2];
     float* g = P.grid + (size_t)(ox + 4 * ah) * sx + (size_t)(oy + 4 * bh) * sy + oz + c;
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a) {
+        float* ga = g + (size_t)a * sx;
+        atomicAdd(ga, acc[a][0].x);
+        atomicAdd(ga + sy, acc[a][0].y);
+        atomicAdd(ga + 2 * sy, acc[a][1].x);
+        atomicAdd(ga + 3 * sy, acc[a][1].y);
+    }
+}
+
+// Contraction of the staged box t4 with NP points per lane: points k and k + 32 (NP = 2, the second
+// only if k + 32 < count). The pair (h^K, h^D) of a grid point is multiplied by duplicated weights in
+// one packed FMA.
+template <int NP, bool WK, bool WD>
+__device__ __forceinline__ void gather_points(const float4* t4, const float4* __restrict__ pts, int k, int count,
+                                              int n, const WinPoly& poly, float* __restrict__ outK,
+                                              float* __restrict__ outD, float sK, float sD, int64_t offK,
+                                              int64_t offD)
+{
+    constexpr int W = 8;
+    float4 p[NP];
+    bool has[NP];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) atomicAdd(g + (size_t)a * sx + (size_t)b * sy, acc[a][b]);
+    for (int i = 0; i < NP; ++i) {
+        has[i] = k + 32 * i < count;
+        p[i] = pts[has[i] ? k + 32 * i : k];
+    }
+    float x[NP][W];
+    float2 y[NP][W], z[NP][W];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        float a[W], b[W];
+        int c;
+        window_weights<W>(poly, p[i].x, n, x[i], &c);
+        window_weights<W>(poly, p[i].y, n, a, &c);
+        window_weights<W>(poly, p[i].z, n, b, &c);
+#pragma unroll
+        for (int q = 0; q < W; ++q) { y[i][q] = f2(a[q], a[q]); z[i][q] = f2(b[q], b[q]); }
+    }
+    float2 f[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) f[i] = f2(0.f, 0.f);          // (K, der) per point
+#pragma unroll 1
+    for (int a = 0; a < W; ++a) {
+        float2 u[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) u[i] = f2(0.f, 0.f);
+        const float4* row = t4 + a * 32;
+#pragma unroll
+        for (int bb = 0; bb < W; ++bb) {
+            float2 s[NP];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) s[i] = f2(0.f, 0.f);
+#pragma unroll
+            for (int cc = 0; cc < W; cc += 2) {
+                const float4 hv = row[(bb * 8 + cc) >> 1];
+                const float2 hc = f2(hv.x, hv.y), hd = f2(hv.z, hv.w);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    s[i] = __ffma2_rn(hc, z[i][cc], s[i]);
+                    s[i] = __ffma2_rn(hd, z[i][cc + 1], s[i]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NP; ++i) u[i] = __ffma2_rn(s[i], y[i][bb], u[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            f[i] = __ffma2_rn(u[i], f2(x[i][0], x[i][0]), f[i]);
+            // rotate so that x[i][0] holds the weight of the next a (keeps indices static)
+#pragma unroll
+            for (int q = 0; q < W - 1; ++q) x[i][q] = x[i][q + 1];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        if (!has[i]) continue;
+        const int64_t idx = (int64_t)__float_as_int(p[i].w);
+        if (WK) outK[idx + offK] = sK * f[i].x;
+        if (WD) outD[idx + offD] = sD * f[i].y;
+    }
 }
 
 // ----------------------------------------------------------------------------------
 // fast 3-D gather, m = 4 (W = 8): lanes own points (two each); the item's box of both grids is
-// staged in shared memory and read back as float4 (h^K_c, h^D_c, h^K_c+1, h^D_c+1), broadcast.
+// staged in shared memory as float2 (h^K, h^D) and read back as float4 (two such pairs). The pair
+// (h^K, h^D) is contracted with duplicated weights in one packed FMA, so each 16-byte broadcast load
+// feeds 4 packed FMAs (8 FMAs) for the lane's two points.
 template <bool WK, bool WD>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_gather3_w8(const int4* __restrict__ items, int nitems,
                                                               const WinDev* __restrict__ wins,
@@ -135,61 +231,14 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_gather3_w8(const int4* __res
     const float sK = WK ? scaleK[it.w] : 0.f;
     const float sD = WD ? scaleD[it.w] : 0.f;
     const int n = P.n;
-    for (int k0 = lane; k0 < it.y; k0 += 64) {
-        const int k1 = k0 + 32;
-        const bool has1 = k1 < it.y;
-        const float4 p0 = pts[k0];
-        const float4 p1 = has1 ? pts[k1] : p0;
-        float x0[W], y0[W], z0[W], x1[W], y1[W], z1[W];
-        int c;
-        window_weights<W>(poly, p0.x, n, x0, &c);
-        window_weights<W>(poly, p0.y, n, y0, &c);
-        window_weights<W>(poly, p0.z, n, z0, &c);
-        window_weights<W>(poly, p1.x, n, x1, &c);
-        window_weights<W>(poly, p1.y, n, y1, &c);
-        window_weights<W>(poly, p1.z, n, z1, &c);
-        float fK0 = 0.f, fD0 = 0.f, fK1 = 0.f, fD1 = 0.f;
-#pragma unroll 1
-        for (int a = 0; a < W; ++a) {
-            float uK0 = 0.f, uD0 = 0.f, uK1 = 0.f, uD1 = 0.f;
-            const float4* row = t4 + a * 32;
-#pragma unroll
-            for (int bb = 0; bb < W; ++bb) {
-                float tK0 = 0.f, tD0 = 0.f, tK1 = 0.f, tD1 = 0.f;
-#pragma unroll
-                for (int cc = 0; cc < W; cc += 2) {
-                    const float4 hv = row[(bb * 8 + cc) >> 1];
-                    tK0 = fmaf(hv.x, z0[cc], tK0);
-                    tD0 = fmaf(hv.y, z0[cc], tD0);
-                    tK1 = fmaf(hv.x, z1[cc], tK1);
-                    tD1 = fmaf(hv.y, z1[cc], tD1);
-                    tK0 = fmaf(hv.z, z0[cc + 1], tK0);
-                    tD0 = fmaf(hv.w, z0[cc + 1], tD0);
-                    tK1 = fmaf(hv.z, z1[cc + 1], tK1);
-                    tD1 = fmaf(hv.w, z1[cc + 1], tD1);
-                }
-                uK0 = fmaf(tK0, y0[bb], uK0);
-                uD0 = fmaf(tD0, y0[bb], uD0);
-                uK1 = fmaf(tK1, y1[bb], uK1);
-                uD1 = fmaf(tD1, y1[bb], uD1);
-            }
-            fK0 = fmaf(uK0, x0[0], fK0);
-            fD0 = fmaf(uD0, x0[0], fD0);
-            fK1 = fmaf(uK1, x1[0], fK1);
-            fD1 = fmaf(uD1, x1[0], fD1);
-            // rotate so that x0[0], x1[0] hold the weights of the next a (keeps indices static)
-#pragma unroll
-            for (int q = 0; q < W - 1; ++q) { x0[q] = x0[q + 1]; x1[q] = x1[q + 1]; }
-        }
-        const int64_t i0 = (int64_t)__float_as_int(p0.w);
-        if (WK) outK[i0 + (int64_t)it.w * strideK] = sK * fK0;
-        if (WD) outD[i0 + (int64_t)it.w * strideD] = sD * fD0;
-        if (has1) {
-            const int64_t i1 = (int64_t)__float_as_int(p1.w);
-            if (WK) outK[i1 + (int64_t)it.w * strideK] = sK * fK1;
-            if (WD) outD[i1 + (int64_t)it.w * strideD] = sD * fD1;
-        }
-    }
+    // two points per lane while more than 32 remain, then one, so tail lanes do no dead work
+    int base = 0;
+    for (; it.y - base > 32; base += 64)
+        gather_points<2, WK, WD>(t4, pts, base + lane, it.y, n, poly, outK, outD, sK, sD,
+                                 (int64_t)it.w * strideK, (int64_t)it.w * strideD);
+    if (base < it.y && base + lane < it.y)
+        gather_points<1, WK, WD>(t4, pts, base + lane, it.y, n, poly, outK, outD, sK, sD,
+                                 (int64_t)it.w * strideK, (int64_t)it.w * strideD);
 }
 
 // ----------------------------------------------------------------------------------
