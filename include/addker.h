@@ -52,6 +52,7 @@ extern "C" {
 #define ADDKER_ENOMEM   -3   /* a device allocation failed */
 #define ADDKER_ECUDA    -4   /* a CUDA runtime call or kernel launch failed */
 #define ADDKER_ETIMEOUT -5   /* a bounded device wait gave up (reserved) */
+#define ADDKER_ELIMIT   -6   /* request larger than the fixed memory of addker_fastsum_noalloc */
 
 /* ---- derivative selectors for addker_dmatvec --------------------------- */
 #define ADDKER_ELL(s)        (s)   /* dK/d ell_s v for window s, 0 <= s < P */
@@ -193,6 +194,35 @@ int addker_profile_read(addker_plan* plan, double* ms, int64_t* launches, int ca
  * `cap` is the capacity of out in doubles. Returns ADDKER_EINVAL if it is too small.
  */
 int addker_debug_stage(addker_plan* plan, int window, int stage, const float* v, double* out, int64_t cap);
+
+/*
+ * The fused product for ONE window without any device allocation. The paper has no counterpart;
+ * this entry point exists for callers that cannot call cudaMalloc: code that runs while a stream is
+ * being captured into a CUDA graph (allocation is not a capturable operation), servers and real-time
+ * loops that forbid device allocation after start-up so their memory use stays fixed, and hosts whose
+ * own allocator owns the device memory. Every working buffer (grids, transform buffers, multipliers,
+ * twiddles, the FP64 coefficient work area) lives in one fixed 9 MiB array in device memory that the
+ * library declares; every GPU that loads the library keeps it until the process exits.
+ *
+ *   points   device, N x d float32 row-major: all d features form the window (1 <= d <= 3), each point
+ *            inside the ball ||x|| <= 1/4 - eps_B/2 with eps_B = 1/16
+ *   ell, sigma_f, bandwidth (M), cutoff (m): as in addker_setup, with oversampling 2, eps_B = 1/16 and
+ *            the default regularisation degree
+ *   v        device, N floats;  Kv, dKdell: device, N floats each (dKdell may be NULL)
+ *            Kv = sigma_f^2 K v,  dKdell = sigma_f^2 (2/ell) K^der v
+ *   stream   cudaStream_t (NULL = legacy default); the call waits for it before returning
+ *
+ * Limit: bandwidth M <= 32 (grid n = 64), d <= 3, any N (points are not sorted, so nothing grows with
+ * N). Larger requests return ADDKER_ELIMIT; malformed ones ADDKER_EINVAL; a point outside the ball or
+ * not finite gives ADDKER_EDOMAIN (outputs then undefined). The first call on a device looks up the
+ * array's device address (once per device, with that device current); make that first call before
+ * any stream capture. All calls share the one array and it keeps the last call's contents (each call
+ * clears what must start at zero): calls that overlap on the GPU, on any stream or thread, race.
+ * No cudaMalloc, cudaFree or other allocating routine is called.
+ */
+int addker_fastsum_noalloc(const float* points, int64_t N, int d, double ell, double sigma_f,
+                           int bandwidth, int cutoff, const float* v, float* Kv, float* dKdell,
+                           void* stream);
 
 #ifdef __cplusplus
 }

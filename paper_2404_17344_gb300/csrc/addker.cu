@@ -726,6 +726,70 @@ int product_one(Plan& p, const float* v, float* Kv, float* dK, int window, int m
 
 }  // namespace
 
+// ---- building blocks for callers that bring their own device memory ---------------------
+namespace addker {
+
+// Window polynomials for cutoff m and oversampling sigma_os.
+void window_poly_for(int m, double sigma_os, WinPoly* poly)
+{
+    fit_window_poly(m, M_PI * (2.0 - 1.0 / sigma_os), poly);
+}
+
+// Fourier multipliers bK, bD, dconv of window w (pointers already set) for length scale ell, computed
+// in the caller's FP64 scratch of at least 4 M^D + M doubles. Enqueued on st and waited for.
+int multipliers_with_scratch(const WinDev& w, double ell, int p_opt, double eps_B, const WinPoly& poly,
+                             double* scratch, cudaStream_t st)
+{
+    const int ps = p_opt >= 0 ? p_opt : std::max(1, (int)std::floor(w.M * eps_B + 0.5));
+    Transition tr;
+    CS(make_transition(ell, ps, eps_B, &tr));
+    int64_t total = 1;
+    for (int t = 0; t < w.D; ++t) total *= w.M;
+    double* a = scratch;
+    double* b = a + total;
+    double* c = b + total;
+    double* d = c + total;
+    double* ph = d + total;
+    double phat[kMaxBandwidth];
+    window_transform(poly, w.m, w.n, w.M, phat);
+    CK(cudaMemcpyAsync(ph, phat, sizeof(double) * w.M, cudaMemcpyHostToDevice, st));
+    const int th = 256, bl = grid_blocks(total, th);
+    if (w.D == 1) k_coef_sample<1><<<bl, th, 0, st>>>(w.M, ell, tr, a, b);
+    else if (w.D == 2) k_coef_sample<2><<<bl, th, 0, st>>>(w.M, ell, tr, a, b);
+    else k_coef_sample<3><<<bl, th, 0, st>>>(w.M, ell, tr, a, b);
+    double* src[2] = {a, b};
+    double* dst[2] = {c, d};
+    for (int t = 0; t < w.D; ++t) {
+        int64_t B = 1, A = 1;
+        for (int u = t + 1; u < w.D; ++u) B *= w.M;
+        for (int u = 0; u < t; ++u) A *= w.M;
+        for (int q = 0; q < 2; ++q) {
+            k_coef_dft<<<bl, th, 0, st>>>(src[q], dst[q], (int)A, w.M, (int)B);
+            std::swap(src[q], dst[q]);
+        }
+    }
+    float* bK = const_cast<float*>(w.bK);
+    float* bD = const_cast<float*>(w.bD);
+    float* dc = const_cast<float*>(w.dconv);
+    if (w.D == 1) k_multipliers<1><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, bK, bD, dc);
+    else if (w.D == 2) k_multipliers<2><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, bK, bD, dc);
+    else k_multipliers<3><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, bK, bD, dc);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    return ADDKER_OK;
+}
+
+// Per-axis twiddles of window w (box and lo set) into tw[t] (forward) and tw[t] + box*M (inverse).
+cudaError_t twiddles_into(const WinDev& w, float2* const tw[3], cudaStream_t st)
+{
+    for (int t = 0; t < w.D; ++t)
+        k_twiddles<<<grid_blocks((int64_t)w.box[t] * w.M, 128), 128, 0, st>>>(tw[t], tw[t] + (int64_t)w.box[t] * w.M,
+                                                                             w.lo[t], w.box[t], w.M, w.n);
+    return cudaGetLastError();
+}
+
+}  // namespace addker
+
 // =================================================================== C ABI ====
 
 extern "C" {
@@ -739,6 +803,8 @@ const char* addker_strerror(int status)
         case ADDKER_ENOMEM: return "device allocation failed";
         case ADDKER_ECUDA: return "CUDA error";
         case ADDKER_ETIMEOUT: return "device wait timed out";
+        case ADDKER_ELIMIT: return "request exceeds the fixed memory limit of addker_fastsum_noalloc "
+                                   "(bandwidth <= 32, at most 3 features)";
         default: return "unknown status";
     }
 }

@@ -138,6 +138,13 @@ cudaError_t launch_spread(const Plan& p, int window_or_all, const float* v, cuda
 cudaError_t launch_gather(const Plan& p, int window_or_all, float* outK, int64_t strideK, float* outD,
                           int64_t strideD, const float* scaleK, const float* scaleD, cudaStream_t st,
                           int* count = nullptr);
+// Building blocks used without a plan (addker_fastsum_noalloc).
+void window_poly_for(int m, double sigma_os, WinPoly* poly);
+int multipliers_with_scratch(const WinDev& w, double ell, int p_opt, double eps_B, const WinPoly& poly,
+                             double* scratch, cudaStream_t st);
+cudaError_t twiddles_into(const WinDev& w, float2* const tw[3], cudaStream_t st);
+cudaError_t launch_transforms_window(const WinDev& w, const WinDev* w_dev, cudaStream_t st);
+
 // grid -> (multiply) -> h for one window or all (window < 0). spec_only: stop after the forward
 // transform and write S_k = G_k dconv_k (the adjoint NFFT) to each window's spec.
 cudaError_t launch_transforms(const Plan& p, int window_or_all, cudaStream_t st, int* count, bool spec_only);

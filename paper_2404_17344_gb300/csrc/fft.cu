@@ -398,4 +398,24 @@ cudaError_t launch_transforms(const Plan& p, int window, cudaStream_t st, int* c
     return cudaGetLastError();
 }
 
+// One window whose descriptor is already in device memory (w_dev) and on the host (w): the same
+// kernels as launch_transforms, without a plan.
+cudaError_t launch_transforms_window(const WinDev& w, const WinDev* w_dev, cudaStream_t st)
+{
+    if (w.D == 3) {
+        ensure_attrs();
+        const int b0 = w.box[0], b1 = w.box[1], b2 = w.box[2], M = w.M;
+        const size_t s1 = sizeof(float2) * (b2 * M + 2 * b1 * M) + sizeof(float) * b1 * b2;
+        const size_t s2 = sizeof(float2) * (b0 * M + b0 * 32) + sizeof(float4) * M * 32;
+        const size_t s3 = sizeof(float4) * (M * M + b1 * M) + sizeof(float2) * (b1 + b2) * M;
+        dim3 g1(b0, 1), g2((M * M + 31) / 32, 1);
+        k_fwd_yz<<<g1, kT, s1, st>>>(w_dev, 0);
+        k_xround<<<g2, kT, s2, st>>>(w_dev, 0, 0);
+        k_inv_yz<<<g1, kT, s3, st>>>(w_dev, 0);
+    } else {
+        generic_window(w, st, false);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace addker

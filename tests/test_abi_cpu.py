@@ -45,7 +45,7 @@ def test_status_codes_match_header():
     from paper_2404_17344_gb300 import native
     text = open(HEADER).read()
     for name in ("ADDKER_OK", "ADDKER_EINVAL", "ADDKER_EDOMAIN", "ADDKER_ENOMEM", "ADDKER_ECUDA",
-                 "ADDKER_ETIMEOUT", "ADDKER_ELL_SHARED", "ADDKER_SIGMA_F", "ADDKER_WIN_KB"):
+                 "ADDKER_ETIMEOUT", "ADDKER_ELIMIT", "ADDKER_ELL_SHARED", "ADDKER_SIGMA_F", "ADDKER_WIN_KB"):
         m = re.search(rf"#define {name}\s+\(?(-?\d+)\)?", text)
         assert m and int(m.group(1)) == getattr(native, name), name
 
