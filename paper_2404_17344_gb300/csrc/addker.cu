@@ -224,13 +224,27 @@ __global__ void k_twiddles(float2* __restrict__ tf, float2* __restrict__ ti, int
 
 // ---------------------------------------------------------------- products ----
 
-__global__ void k_window_sum(const float* __restrict__ ks, int P, int64_t N, float scale, float* __restrict__ out)
+// out[i] = scale sum_s ks[s N + i]; four consecutive i per thread (16-byte accesses when vec: N % 4 == 0
+// and out 16-byte aligned)
+__global__ void k_window_sum(const float* __restrict__ ks, int P, int64_t N, float scale, float* __restrict__ out,
+                             int vec)
 {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    float acc = 0.f;
-    for (int s = 0; s < P; ++s) acc += ks[(int64_t)s * N + i];
-    out[i] = scale * acc;
+    const int64_t i0 = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+    if (i0 >= N) return;
+    if (vec) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int s = 0; s < P; ++s) {
+            const float4 k = *reinterpret_cast<const float4*>(ks + (int64_t)s * N + i0);
+            acc.x += k.x; acc.y += k.y; acc.z += k.z; acc.w += k.w;
+        }
+        *reinterpret_cast<float4*>(out + i0) = make_float4(scale * acc.x, scale * acc.y, scale * acc.z, scale * acc.w);
+        return;
+    }
+    for (int64_t i = i0; i < i0 + 4 && i < N; ++i) {
+        float acc = 0.f;
+        for (int s = 0; s < P; ++s) acc += ks[(int64_t)s * N + i];
+        out[i] = scale * acc;
+    }
 }
 
 __global__ void k_max_norm(const float* __restrict__ X, int64_t N, int d, const int* __restrict__ off,
@@ -582,6 +596,7 @@ int setup_window(Plan& p, int s, const float* X, int* keys, int* flag, std::vect
     float4 *b1 = nullptr, *b2 = nullptr, *spec;
     float* mult;
     CS(dalloc(p, &grid, gsz));
+    CK(cudaMemset(grid, 0, sizeof(float) * gsz));
     CS(dalloc(p, &hh, gsz));
     if (D == 3) {
         CS(dalloc(p, &b1, (int64_t)w.box[0] * std::max(w.box[1], M) * M));
@@ -657,6 +672,11 @@ struct Stage {                            // brackets one stage of a product wit
     }
 };
 
+int vec_ok(const Plan& p, const float* out)
+{
+    return (p.N % 4 == 0) && (reinterpret_cast<uintptr_t>(out) % 16 == 0);
+}
+
 // One product for one right-hand side.
 //   mode 0: Kv = K v (if Kv) and dK[s] = dK/d ell_s v for all s (if dK; stride N)
 //   mode 1: dK = dK/d ell_s v for the single window `window`
@@ -666,10 +686,13 @@ int product_one(Plan& p, const float* v, float* Kv, float* dK, int window, int m
     cudaStream_t st = p.stream;
     const int only = mode == 1 ? window : -1;
     {
+        // d = 3 grids are zeroed by the forward transform that consumes them (and at setup); the
+        // generic d < 3 path clears here
         Stage sg(p, 0);
         for (int s = 0; s < p.P; ++s) {
             if (only >= 0 && s != only) continue;
             const WinDev& w = p.win[s];
+            if (w.D == 3) continue;
             CK(cudaMemsetAsync(w.grid, 0, sizeof(float) * (size_t)w.box[0] * w.box[1] * w.box[2], st));
         }
         sg.done(0);
@@ -705,7 +728,7 @@ int product_one(Plan& p, const float* v, float* Kv, float* dK, int window, int m
         CK(launch_gather(p, -1, nullptr, 0, p.ks, p.N, ones, sder, st, &n));
         sg.done(n);
         Stage sum(p, 4);
-        k_window_sum<<<grid_blocks(p.N, 256), 256, 0, st>>>(p.ks, p.P, p.N, 1.0f, Kv);
+        k_window_sum<<<grid_blocks((p.N + 3) / 4, 256), 256, 0, st>>>(p.ks, p.P, p.N, 1.0f, Kv, vec_ok(p, Kv));
         CK(cudaGetLastError());
         sum.done(1);
         return ADDKER_OK;
@@ -718,7 +741,8 @@ int product_one(Plan& p, const float* v, float* Kv, float* dK, int window, int m
     CK(launch_gather(p, -1, p.ks, p.N, dK, p.N, ones, sder, st, &n));
     sg.done(n);
     Stage sum(p, 4);
-    k_window_sum<<<grid_blocks(p.N, 256), 256, 0, st>>>(p.ks, p.P, p.N, (float)(p.sigma_f * p.sigma_f), Kv);
+    k_window_sum<<<grid_blocks((p.N + 3) / 4, 256), 256, 0, st>>>(p.ks, p.P, p.N, (float)(p.sigma_f * p.sigma_f), Kv,
+                                                                   vec_ok(p, Kv));
     CK(cudaGetLastError());
     sum.done(1);
     return ADDKER_OK;
@@ -1124,6 +1148,7 @@ int addker_debug_stage(addker_plan* plan, int window, int stage, const float* v,
     if (stage == 0) {
         std::vector<float> g(gsz);
         CK(cudaMemcpyAsync(g.data(), w.grid, sizeof(float) * gsz, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemsetAsync(w.grid, 0, sizeof(float) * gsz, st));        // products expect a zeroed grid
         CK(cudaStreamSynchronize(st));
         // the device window is w = phi * C with C = pi m / sinh(b m); report in phi's normalisation
         double b = M_PI * (2.0 - 1.0 / p.sigma_os);
@@ -1141,6 +1166,7 @@ int addker_debug_stage(addker_plan* plan, int window, int stage, const float* v,
         return ADDKER_OK;
     }
     CK(launch_transforms(p, window, st, nullptr, true));
+    CK(cudaMemsetAsync(w.grid, 0, sizeof(float) * gsz, st));            // d < 3 passes do not consume it
     std::vector<float4> s(md);
     CK(cudaMemcpyAsync(s.data(), w.spec, sizeof(float4) * md, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

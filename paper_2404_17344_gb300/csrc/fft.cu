@@ -40,6 +40,7 @@ constexpr int kT = 256;
 
 // block = (x, window). smem: gs[b1][b2] float, tz[b2][M], ty[b1][M], t1[b1][M] float2.
 //   t1[y][kz] = sum_z g[x][y][z] tz[z][kz];   out[x][ky][kz] = sum_y ty[y][ky] t1[y][kz]
+// The grid slab is zeroed once read, so d = 3 grids need no separate clearing before a spread.
 __global__ void __launch_bounds__(kT) k_fwd_yz(const WinDev* __restrict__ wins, int w0)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -52,8 +53,11 @@ __global__ void __launch_bounds__(kT) k_fwd_yz(const WinDev* __restrict__ wins, 
     float2* ty = tz + b2 * M;
     float2* t1 = ty + b1 * M;
     float* gs = reinterpret_cast<float*>(t1 + b1 * M);
-    const float* g = W.grid + (size_t)x * b1 * b2;
-    for (int i = threadIdx.x; i < b1 * b2; i += kT) gs[i] = g[i];
+    float* g = W.grid + (size_t)x * b1 * b2;
+    for (int i = threadIdx.x; i < b1 * b2; i += kT) {
+        gs[i] = g[i];
+        g[i] = 0.f;                      // the slab is consumed: leave the grid zeroed for the next spread
+    }
     for (int i = threadIdx.x; i < b2 * M; i += kT) tz[i] = W.twf[2][i];
     for (int i = threadIdx.x; i < b1 * M; i += kT) ty[i] = W.twf[1][i];
     __syncthreads();
