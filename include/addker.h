@@ -143,6 +143,22 @@ int addker_matvec_all(addker_plan* plan, const float* v, float* Kv, float* dKdel
  */
 int addker_matvec_all_host(addker_plan* plan, const float* v, float* Kv, float* dKdell, int nrhs);
 
+/*
+ * Vector-Jacobian product of the product K v: the gradients of f = w^T K v (K the operator as the
+ * fast summation computes it, Sec. 3.1 and 3.3) with respect to v, the hyperparameters and the points.
+ *   v, w         device, N floats each
+ *   grad_v       device, N floats: K w  (K is symmetric)
+ *   grad_theta   device, P + 1 doubles: w^T (dK/d ell_s) v for s = 0..P-1, then w^T (dK/d sigma_f) v
+ *   grad_points  device, N x d floats, row-major like `points`: df/dx (a feature used by several
+ *                windows gets the sum of their contributions); must not be NULL
+ * The coordinate gradient differentiates the interpolation window (the NFFT's last step) at the
+ * target point; with f = w^T A B A^T v it is w_k grad(A h(v))_k + v_k grad(A h(w))_k per window.
+ * Nothing from earlier products is kept: the grids of v and of w are computed here (two spreads,
+ * two sets of transforms). Enqueued on the plan's stream; uses the plan's window-sum scratch.
+ */
+int addker_vjp(addker_plan* plan, const float* v, const float* w, float* grad_v, double* grad_theta,
+               float* grad_points);
+
 /* Wait for the plan's stream; report a failed kernel as ADDKER_ECUDA. */
 int addker_sync(addker_plan* plan);
 

@@ -41,6 +41,10 @@ def lib():
             L.orc_spread.restype = None
             L.orc_gather.argtypes = [i64, i32, P, i32, i32, f64, i32, P, P]
             L.orc_gather.restype = None
+            L.orc_direct_grad_x.argtypes = [i64, i32, P, i32, P, P, P, f64, P, P, i64, P, P]
+            L.orc_direct_grad_x.restype = None
+            L.orc_gather_grad.argtypes = [i64, i32, P, i32, i32, f64, P, P, P]
+            L.orc_gather_grad.restype = None
             L.orc_num_threads.argtypes = []
             L.orc_num_threads.restype = i32
             _lib = L

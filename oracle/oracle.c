@@ -14,6 +14,10 @@
  *                 inner sum of eq. "approx fast sum" computed approximately).
  *  orc_gather   : the interpolation step of the NFFT,
  *                 f_i = sum_l h_l phi~(x_i - l/n) (Sec. 3.1, the outer sum).
+ *  orc_direct_grad_x : the gradient of w^T K v with respect to the points, from
+ *                 the kernel's definition.
+ *  orc_gather_grad : the interpolation and its gradient in the target point
+ *                 (the window differentiated).
  *
  * phi is the Kaiser-Bessel window with shape b and cutoff m on a grid of n
  * points per dimension:
@@ -181,5 +185,108 @@ void orc_gather(int64_t N, int D, const double *x, int n, int m, double b, int n
             }
             out[(size_t)q * (size_t)N + i] = s;
         }
+    }
+}
+
+/*
+ * Gradient of f = w^T K v with respect to the points, straight from the definition (Sec. 3.3 kernel):
+ *   df/dx_{k,f} = sigma_f^2 sum_{s: f in W_s} sum_j (w_k v_j + w_j v_k) * (-(x_{k,f} - x_{j,f}) / ell_s^2)
+ *                 * exp(-|x_k^W - x_j^W|^2 / (2 ell_s^2))
+ * for rows k in rows[0..nrows); out is nrows x d (zero for features in no window).
+ */
+void orc_direct_grad_x(int64_t N, int d, const float *X, int P, const int *win_off, const int *win_feat,
+                       const double *ell, double sigma_f, const double *v, const double *w, int64_t nrows,
+                       const int64_t *rows, double *out)
+{
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t r = 0; r < nrows; ++r) {
+        int64_t k = rows[r];
+        for (int f = 0; f < d; ++f) out[r * d + f] = 0.0;
+        for (int s = 0; s < P; ++s) {
+            double e2 = 2.0 * ell[s] * ell[s];
+            double l2 = ell[s] * ell[s];
+            for (int64_t j = 0; j < N; ++j) {
+                double r2 = 0.0;
+                for (int q = win_off[s]; q < win_off[s + 1]; ++q) {
+                    int f = win_feat[q];
+                    double diff = (double)X[k * d + f] - (double)X[j * d + f];
+                    r2 += diff * diff;
+                }
+                double kv = exp(-r2 / e2) * (w[k] * v[j] + w[j] * v[k]);
+                for (int q = win_off[s]; q < win_off[s + 1]; ++q) {
+                    int f = win_feat[q];
+                    double diff = (double)X[k * d + f] - (double)X[j * d + f];
+                    out[r * d + f] += sigma_f * sigma_f * (-diff / l2) * kv;
+                }
+            }
+        }
+    }
+}
+
+/* d/dt of the Kaiser-Bessel window kb(t) (t = n x), from kb = sinh(b s)/(pi s), s = sqrt(m^2 - t^2):
+ *   dkb/dt = (-t/s) (b cosh(b s)/(pi s) - sinh(b s)/(pi s^2)),  -> -t b^3/(3 pi) as s -> 0. */
+static double kb_dt(double t, int m, double b)
+{
+    double s2 = (double)m * (double)m - t * t;
+    if (s2 < 0.0) return 0.0;
+    double s = sqrt(s2);
+    if (s < 1e-4) return -t * b * b * b / (3.0 * ORC_PI) * (1.0 + b * b * s2 / 10.0);
+    return (-t / s) * (b * cosh(b * s) / (ORC_PI * s) - sinh(b * s) / (ORC_PI * s * s));
+}
+
+/*
+ * Interpolation and its gradient (the NFFT's last step, differentiated in the target point):
+ *   val[i]        = sum_l h_l prod_t phi~(x_{i,t} - l_t/n)
+ *   grad[i*D + t] = sum_l h_l phi~'(x_{i,t} - l_t/n) prod_{u != t} phi~(x_{i,u} - l_u/n)
+ * with phi' = n dkb/dt. One grid h (n^D values).
+ */
+void orc_gather_grad(int64_t N, int D, const double *x, int n, int m, double b, const double *h, double *val,
+                     double *grad)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t idx[3][64];
+        double w[3][64], dw[3][64];
+        for (int t = 0; t < D; ++t) {
+            double u = x[i * D + t] * n;
+            double fl = floor(u);
+            for (int q = 0; q < 2 * m; ++q) {
+                double l = fl - m + 1 + q;
+                w[t][q] = kb(u - l, m, b);
+                dw[t][q] = n * kb_dt(u - l, m, b);
+                int64_t a = ((int64_t)l + n / 2) % n;
+                if (a < 0) a += n;
+                idx[t][q] = a;
+            }
+        }
+        int W = 2 * m;
+        double s = 0.0, g[3] = {0.0, 0.0, 0.0};
+        if (D == 1) {
+            for (int a = 0; a < W; ++a) {
+                double hv = h[idx[0][a]];
+                s += hv * w[0][a];
+                g[0] += hv * dw[0][a];
+            }
+        } else if (D == 2) {
+            for (int a = 0; a < W; ++a)
+                for (int c = 0; c < W; ++c) {
+                    double hv = h[idx[0][a] * n + idx[1][c]];
+                    s += hv * w[0][a] * w[1][c];
+                    g[0] += hv * dw[0][a] * w[1][c];
+                    g[1] += hv * w[0][a] * dw[1][c];
+                }
+        } else {
+            for (int a = 0; a < W; ++a)
+                for (int c = 0; c < W; ++c)
+                    for (int e = 0; e < W; ++e) {
+                        double hv = h[(idx[0][a] * n + idx[1][c]) * n + idx[2][e]];
+                        s += hv * w[0][a] * w[1][c] * w[2][e];
+                        g[0] += hv * dw[0][a] * w[1][c] * w[2][e];
+                        g[1] += hv * w[0][a] * dw[1][c] * w[2][e];
+                        g[2] += hv * w[0][a] * w[1][c] * dw[2][e];
+                    }
+        }
+        val[i] = s;
+        for (int t = 0; t < D; ++t) grad[i * D + t] = g[t];
     }
 }

@@ -150,6 +150,23 @@ class AddKer:
                                               ctypes.c_void_p(dK.data_ptr()) if dK is not None else None, int(nrhs)),
                      "addker_matvec_all_host")
 
+    def vjp(self, v, w):
+        """Gradients of f = w^T K v: (K w [N], grad_theta [P + 1] float64 = (df/d ell_s..., df/d sigma_f),
+        df/dpoints [N, d]). v and w are (N,) float32 CUDA tensors."""
+        torch = _torch()
+        L = self._ready()
+        v = _dev_f32(v, "v")
+        w = _dev_f32(w, "w")
+        if v.shape != (self.N,) or w.shape != (self.N,):
+            raise ValueError("v and w must be (N,)")
+        gv = torch.empty(self.N, device=v.device, dtype=torch.float32)
+        gt = torch.empty(self.P + 1, device=v.device, dtype=torch.float64)
+        gx = torch.empty(self.N, self.d, device=v.device, dtype=torch.float32)
+        native.check(L.addker_vjp(self._plan, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(w.data_ptr()),
+                                  ctypes.c_void_p(gv.data_ptr()), ctypes.c_void_p(gt.data_ptr()),
+                                  ctypes.c_void_p(gx.data_ptr())), "addker_vjp")
+        return gv, gt, gx
+
     # -- plan management ---------------------------------------------------------------------
     def set_params(self, ell=None, sigma_f=None):
         L = self._ready()

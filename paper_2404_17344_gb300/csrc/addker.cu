@@ -247,6 +247,22 @@ __global__ void k_window_sum(const float* __restrict__ ks, int P, int64_t N, flo
     }
 }
 
+struct ThetaScale {
+    double s[2 * kMaxWindows + 1];       // [0,P): sigma_f^2 2/ell_s ; P: 2 sigma_f
+};
+
+// grad_theta[s] = sigma_f^2 (2/ell_s) dots[P + s]  (s < P);  grad_theta[P] = 2 sigma_f sum_s dots[s]
+__global__ void k_theta_grad(const double* __restrict__ dots, int P, ThetaScale sc, double* __restrict__ out)
+{
+    const int s = threadIdx.x;
+    if (s < P) out[s] = sc.s[s] * dots[P + s];
+    if (s == 0) {
+        double acc = 0.0;
+        for (int q = 0; q < P; ++q) acc += dots[q];
+        out[P] = sc.s[P] * acc;
+    }
+}
+
 __global__ void k_max_norm(const float* __restrict__ X, int64_t N, int d, const int* __restrict__ off,
                            const int* __restrict__ feat, int P, unsigned* __restrict__ result)
 {
@@ -518,6 +534,7 @@ int setup_window(Plan& p, int s, const float* X, int* keys, int* flag, std::vect
     const int D = w.D, n = w.n;
     int f[3] = {0, 0, 0};
     for (int t = 0; t < D; ++t) f[t] = p.feat[p.feat_off[s] + t];
+    for (int t = 0; t < 3; ++t) w.feat[t] = f[t];
     int64_t cells = 1;
     for (int t = 0; t < D; ++t) cells *= n;
     int* hist = nullptr;
@@ -936,6 +953,7 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
     if (status == ADDKER_OK) status = dalloc(p, &p.wins_dev, P);
     if (status == ADDKER_OK && P > 1) status = dalloc(p, &p.ks, (int64_t)P * N);
     if (status == ADDKER_OK) status = dalloc(p, &p.scale_dev, 3 * P);
+    if (status == ADDKER_OK) status = dalloc(p, &p.dots, 2 * P);
     for (int s = 0; s < P && status == ADDKER_OK; ++s) status = compute_multipliers(p, s);
     if (status == ADDKER_OK && cudaMemcpy(p.wins_dev, p.win.data(), sizeof(WinDev) * P, cudaMemcpyHostToDevice) != cudaSuccess)
         status = ADDKER_ECUDA;
@@ -1005,6 +1023,44 @@ int addker_dmatvec(addker_plan* plan, int param, const float* v, float* out, int
             CS(product_one(p, vj, oj, nullptr, -1, 2));
         }
     }
+    return ADDKER_OK;
+}
+
+int addker_vjp(addker_plan* plan, const float* v, const float* w, float* grad_v, double* grad_theta,
+               float* grad_points)
+{
+    if (!plan || !v || !w || !grad_v || !grad_theta || !grad_points) return ADDKER_EINVAL;
+    Plan& p = plan->p;
+    cudaStream_t st = p.stream;
+    float* gx = grad_points;
+    CK(cudaMemsetAsync(gx, 0, sizeof(float) * (size_t)p.N * p.d, st));
+    CK(cudaMemsetAsync(p.dots, 0, sizeof(double) * 2 * p.P, st));
+    // scratch for the per-window f^K of w: the plan's window-sum buffer (N for P = 1 is grad_v itself)
+    float* ks = p.P > 1 ? p.ks : grad_v;
+    for (int pass = 0; pass < 2; ++pass) {
+        const float* u = pass == 0 ? w : v;
+        for (int s = 0; s < p.P; ++s) {
+            const WinDev& wd = p.win[s];
+            if (wd.D != 3) CK(cudaMemsetAsync(wd.grid, 0, sizeof(float) * (size_t)wd.box[0] * wd.box[1] * wd.box[2], st));
+        }
+        CK(launch_spread(p, -1, u, st, nullptr));
+        CK(launch_transforms(p, -1, st, nullptr, false));
+        CK(launch_gather_grad(p, pass, pass == 0 ? v : w, ks, gx, st, nullptr));
+        if (pass == 0) {
+            if (p.P > 1)
+                k_window_sum<<<grid_blocks((p.N + 3) / 4, 256), 256, 0, st>>>(p.ks, p.P, p.N,
+                                                                               (float)(p.sigma_f * p.sigma_f), grad_v,
+                                                                               vec_ok(p, grad_v));
+            else
+                k_scale<<<grid_blocks(p.N, 256), 256, 0, st>>>(grad_v, p.N, (float)(p.sigma_f * p.sigma_f), grad_v);
+            CK(cudaGetLastError());
+        }
+    }
+    ThetaScale sc;
+    for (int s = 0; s < p.P; ++s) sc.s[s] = p.sigma_f * p.sigma_f * 2.0 / p.ell[s];
+    sc.s[p.P] = 2.0 * p.sigma_f;
+    k_theta_grad<<<1, 64, 0, st>>>(p.dots, p.P, sc, grad_theta);
+    CK(cudaGetLastError());
     return ADDKER_OK;
 }
 

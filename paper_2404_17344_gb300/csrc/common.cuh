@@ -56,6 +56,7 @@ struct WinDev {                          // copied by value into kernel paramete
     const float2* twf[3];                // [axis]: box[axis] x M
     const float2* twi[3];                // [axis]: M x box[axis]
     int D, M, n, m;
+    int feat[3];                         // feature (column of the points array) of each axis
     int lo[3];                           // grid-array index (l + n/2) of the box origin per axis
     int box[3];
     float b;                             // Kaiser-Bessel shape pi (2 - 1/sigma)
@@ -91,6 +92,7 @@ struct Plan {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
     int64_t launches[5] = {0, 0, 0, 0, 0};
+    double* dots = nullptr;               // 2P doubles: gradient dot products (addker_vjp)
 };
 
 // ---- device window weights ------------------------------------------------------------
@@ -130,6 +132,37 @@ __device__ __forceinline__ void window_weights_n(const WinPoly& P, float x, int 
     for (int q = 0; q < W / 2; ++q) window_pair(P, q, u, u2, &w[q], &w[W - 1 - q]);
 }
 
+// Weights and their x-derivatives: dw_q = dP_q/du * du/dx with du/dx = 2n. For the mirrored pair,
+// with A = 2u E'(u^2) and B = O(u^2) + 2u^2 O'(u^2): dP_q/du = A + B and dP_{W-1-q}/du = A - B.
+__device__ __forceinline__ void window_weights_grad_n(const WinPoly& P, float x, int n, int W, float* w, float* dw,
+                                                      int* cell)
+{
+    const float s = x * (float)n;
+    const float fl = floorf(s);
+    const float u = 2.0f * (s - fl) - 1.0f;
+    const float u2 = u * u;
+    const float dudx = 2.0f * (float)n;
+    *cell = (int)fl + n / 2;
+    for (int q = 0; q < W / 2; ++q) {
+        float E = P.e[q][kHalfCoef - 1], O = P.o[q][kHalfCoef - 1];
+        float dE = (kHalfCoef - 1) * P.e[q][kHalfCoef - 1], dO = (kHalfCoef - 1) * P.o[q][kHalfCoef - 1];
+        for (int i = kHalfCoef - 2; i >= 0; --i) {
+            E = fmaf(E, u2, P.e[q][i]);
+            O = fmaf(O, u2, P.o[q][i]);
+            if (i >= 1) {
+                dE = fmaf(dE, u2, (float)i * P.e[q][i]);
+                dO = fmaf(dO, u2, (float)i * P.o[q][i]);
+            }
+        }
+        w[q] = fmaf(u, O, E);
+        w[W - 1 - q] = fmaf(-u, O, E);
+        const float A = 2.0f * u * dE;
+        const float B = fmaf(2.0f * u2, dO, O);
+        dw[q] = (A + B) * dudx;
+        dw[W - 1 - q] = (A - B) * dudx;
+    }
+}
+
 // ---- launchers implemented in the other translation units -------------------------
 // Each launcher returns the number of kernels it launched through *count (may be NULL).
 cudaError_t launch_spread(const Plan& p, int window_or_all, const float* v, cudaStream_t st, int* count = nullptr);
@@ -138,6 +171,13 @@ cudaError_t launch_spread(const Plan& p, int window_or_all, const float* v, cuda
 cudaError_t launch_gather(const Plan& p, int window_or_all, float* outK, int64_t strideK, float* outD,
                           int64_t strideD, const float* scaleK, const float* scaleD, cudaStream_t st,
                           int* count = nullptr);
+// Gradient gathers of addker_vjp (gradients.cu). Pass 0 reads the grids of w: writes f^K to
+// ks[s N + i], accumulates dots[s] += v_i f^K, dots[P + s] += v_i f^D and
+// grad_x[i d + feat] += sigma_f^2 v_i grad f^K. Pass 1 reads the grids of v and accumulates
+// grad_x[i d + feat] += sigma_f^2 w_i grad f^K.
+cudaError_t launch_gather_grad(const Plan& p, int pass, const float* other, float* ks, float* grad_x,
+                               cudaStream_t st, int* count);
+
 // Building blocks used without a plan (addker_fastsum_noalloc).
 void window_poly_for(int m, double sigma_os, WinPoly* poly);
 int multipliers_with_scratch(const WinDev& w, double ell, int p_opt, double eps_B, const WinPoly& poly,

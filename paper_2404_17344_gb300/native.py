@@ -51,6 +51,7 @@ SIGNATURES = {
     "addker_info": (_I, [_VP, ctypes.POINTER(_I64), _I]),
     "addker_debug_stage": (_I, [_VP, _I, _I, _VP, _VP, _I64]),
     "addker_profile": (_I, [_VP, _I]),
+    "addker_vjp": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "addker_fastsum_noalloc": (_I, [_VP, _I64, _I, _D, _D, _I, _I, _VP, _VP, _VP, _VP]),
     "addker_profile_read": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I]),
 }
