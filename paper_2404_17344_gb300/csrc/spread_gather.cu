@@ -242,6 +242,160 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_gather3_w8(const int4* __res
 }
 
 // ----------------------------------------------------------------------------------
+// fast 1-D and 2-D kernels, m = 4 (W = 8): one warp per work item, lanes own points. The spread
+// accumulates the item's whole support box (8 or 8x8 values) in each lane's registers and reduces it
+// across the warp once per item (a transpose-reduction: each halving step trades half of a lane's
+// values with its partner), so no atomics touch a grid value more than once per item.
+
+// Sum each of the NV entries v[0..NV) over the 32 lanes of the warp (NV a power of two <= 64) by
+// recursive halving: at offset off a lane swaps half of its current entries with lane ^ off, keeping the
+// lower half if bit off is clear and the upper half otherwise. Afterwards v[0..held) are complete totals of
+// entries base .. base + held - 1, with held = max(1, NV / 32); for NV < 32 each entry is held by
+// 32 / NV lanes (those equal in the bits used for halving).
+template <int NV>
+__device__ __forceinline__ void warp_transpose_reduce(float* v, int lane, int* base_out, int* held_out)
+{
+    int held = NV;
+    int base = 0;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        if (held == 1) {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+            continue;
+        }
+        const int half = held / 2;
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < NV / 2; ++i) {
+            if (i < half) {
+                const float send = upper ? v[i] : v[i + half];
+                const float keep = upper ? v[i + half] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+            }
+        }
+        if (upper) base += half;
+        held = half;
+    }
+    *base_out = base;
+    *held_out = held;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kWarps * 32) k_spread_lowd_w8(const int4* __restrict__ items, int nitems,
+                                                               const WinDev* __restrict__ wins,
+                                                               const float* __restrict__ v, const WinPoly poly)
+{
+    constexpr int W = 8;
+    constexpr int NV = D == 1 ? W : W * W;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * kWarps + warp;
+    if (item >= nitems) return;
+    const int4 it = items[item];
+    const WinDev& P = wins[it.w];
+    const float4* __restrict__ pts = P.pts + it.x;
+    float acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.f;
+    for (int k = lane; k < it.y; k += 32) {
+        const float4 p = pts[k];
+        const float vv = __ldg(v + __float_as_int(p.w));
+        float wx[W];
+        int c;
+        window_weights<W>(poly, p.x, P.n, wx, &c);
+        if (D == 1) {
+#pragma unroll
+            for (int a = 0; a < W; ++a) acc[a] = fmaf(vv, wx[a], acc[a]);
+        } else {
+            float wy[W];
+            window_weights<W>(poly, p.y, P.n, wy, &c);
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                const float xa = vv * wx[a];
+#pragma unroll
+                for (int b = 0; b < W; b += 2) {
+                    float2 t = make_float2(acc[a * W + b], acc[a * W + b + 1]);
+                    t = __ffma2_rn(make_float2(xa, xa), make_float2(wy[b], wy[b + 1]), t);
+                    acc[a * W + b] = t.x;
+                    acc[a * W + b + 1] = t.y;
+                }
+            }
+        }
+    }
+    int base, held;
+    warp_transpose_reduce<NV>(acc, lane, &base, &held);
+    const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff;
+    const int ox = cx - 3 - P.lo[0], oy = cy - 3 - P.lo[1];
+    // for NV < 32 several lanes hold the same total: the lowest of them adds it
+    const bool first = NV >= 32 || (lane & (32 / NV - 1)) == 0;
+    if (first) {
+#pragma unroll
+        for (int e = 0; e < (NV >= 32 ? NV / 32 : 1); ++e) {
+            const int idx = base + e;
+            const int a = D == 1 ? idx : idx / W, b = D == 1 ? 0 : idx % W;
+            atomicAdd(P.grid + (size_t)(ox + a) * P.box[1] + (D >= 2 ? oy + b : 0), acc[e]);
+        }
+    }
+}
+
+template <int D, bool WK, bool WD>
+__global__ void __launch_bounds__(kWarps * 32) k_gather_lowd_w8(const int4* __restrict__ items, int nitems,
+                                                               const WinDev* __restrict__ wins,
+                                                               float* __restrict__ outK, float* __restrict__ outD,
+                                                               const float* __restrict__ scaleK,
+                                                               const float* __restrict__ scaleD, int64_t strideK,
+                                                               int64_t strideD, const WinPoly poly)
+{
+    constexpr int W = 8;
+    constexpr int NV = D == 1 ? W : W * W;
+    __shared__ __align__(16) float2 tile[kWarps][NV];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * kWarps + warp;
+    if (item >= nitems) return;
+    const int4 it = items[item];
+    const WinDev& P = wins[it.w];
+    const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff;
+    const int ox = cx - 3 - P.lo[0], oy = cy - 3 - P.lo[1];
+    float2* t = tile[warp];
+    for (int i = lane; i < NV; i += 32) {
+        const int a = D == 1 ? i : i / W, b = D == 1 ? 0 : i % W;
+        t[i] = P.h[(size_t)(ox + a) * P.box[1] + (D >= 2 ? oy + b : 0)];
+    }
+    __syncwarp();
+    const float4* __restrict__ pts = P.pts + it.x;
+    const float sK = WK ? scaleK[it.w] : 0.f;
+    const float sD = WD ? scaleD[it.w] : 0.f;
+    for (int k = lane; k < it.y; k += 32) {
+        const float4 p = pts[k];
+        float wx[W];
+        int c;
+        window_weights<W>(poly, p.x, P.n, wx, &c);
+        float2 f = make_float2(0.f, 0.f);
+        if (D == 1) {
+#pragma unroll
+            for (int a = 0; a < W; ++a) f = __ffma2_rn(t[a], make_float2(wx[a], wx[a]), f);
+        } else {
+            float wy[W];
+            window_weights<W>(poly, p.y, P.n, wy, &c);
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                float2 u = make_float2(0.f, 0.f);
+                const float4* row = reinterpret_cast<const float4*>(t + a * W);
+#pragma unroll
+                for (int b = 0; b < W; b += 2) {
+                    const float4 hv = row[b / 2];
+                    u = __ffma2_rn(make_float2(hv.x, hv.y), make_float2(wy[b], wy[b]), u);
+                    u = __ffma2_rn(make_float2(hv.z, hv.w), make_float2(wy[b + 1], wy[b + 1]), u);
+                }
+                f = __ffma2_rn(u, make_float2(wx[a], wx[a]), f);
+            }
+        }
+        const int64_t i = (int64_t)__float_as_int(p.w);
+        if (WK) outK[i + (int64_t)it.w * strideK] = sK * f.x;
+        if (WD) outD[i + (int64_t)it.w * strideD] = sD * f.y;
+    }
+}
+
+// ----------------------------------------------------------------------------------
 // generic kernels: any D in {1,2,3}, W = 2m <= 16. One block per item; the spread accumulates
 // the item's W^D support box in shared memory, then adds it to the grid.
 template <int D>
@@ -360,7 +514,10 @@ cudaError_t launch_spread(const Plan& p, int window, const float* v, cudaStream_
         const int n = gb[s + 1] - gb[s];
         if (n == 0) continue;
         const int4* it = p.items_gen + gb[s];
-        switch (p.dims[s]) {
+        const int nb = (n + kWarps - 1) / kWarps;
+        if (p.m == 4 && p.dims[s] == 1) k_spread_lowd_w8<1><<<nb, kWarps * 32, 0, st>>>(it, n, wd, v, p.poly);
+        else if (p.m == 4 && p.dims[s] == 2) k_spread_lowd_w8<2><<<nb, kWarps * 32, 0, st>>>(it, n, wd, v, p.poly);
+        else switch (p.dims[s]) {
             case 1: k_spread_generic<1><<<n, 128, 0, st>>>(it, wd, v, p.poly); break;
             case 2: k_spread_generic<2><<<n, 128, 0, st>>>(it, wd, v, p.poly); break;
             default: k_spread_generic<3><<<n, 128, 0, st>>>(it, wd, v, p.poly); break;
@@ -391,7 +548,12 @@ static int gather_all(const Plan& p, int window, float* outK, int64_t zK, float*
         const int n = gb[s + 1] - gb[s];
         if (n == 0) continue;
         const int4* it = p.items_gen + gb[s];
-        switch (p.dims[s]) {
+        const int nb = (n + kWarps - 1) / kWarps;
+        if (p.m == 4 && p.dims[s] == 1)
+            k_gather_lowd_w8<1, WK, WD><<<nb, kWarps * 32, 0, st>>>(it, n, wd, outK, outD, sK, sD, zK, zD, p.poly);
+        else if (p.m == 4 && p.dims[s] == 2)
+            k_gather_lowd_w8<2, WK, WD><<<nb, kWarps * 32, 0, st>>>(it, n, wd, outK, outD, sK, sD, zK, zD, p.poly);
+        else switch (p.dims[s]) {
             case 1: k_gather_generic<1, WK, WD><<<n, 128, 0, st>>>(it, wd, outK, outD, sK, sD, zK, zD, p.poly); break;
             case 2: k_gather_generic<2, WK, WD><<<n, 128, 0, st>>>(it, wd, outK, outD, sK, sD, zK, zD, p.poly); break;
             default: k_gather_generic<3, WK, WD><<<n, 128, 0, st>>>(it, wd, outK, outD, sK, sD, zK, zD, p.poly); break;
