@@ -117,6 +117,16 @@ int addker_set_stream(addker_plan* plan, void* stream);
 /*
  * Kv = K v. v and Kv: device, N x nrhs float32, column-major (column j is
  * right-hand side j, leading dimension N). nrhs >= 1.
+ *
+ * Batches (all product entry points): right-hand sides are processed up to eight
+ * at a time, each stage one launch per kernel kind for the whole group, every
+ * right-hand side with its own grid slot. The plan allocates slots on demand: the
+ * first call with a larger nrhs (up to 8, rounded up to a power of two)
+ * synchronises the plan's stream and grows the per-window grid memory by that
+ * factor. If that allocation fails the call runs one right-hand side at a
+ * time instead (ADDKER_ENOMEM only if even one slot cannot be allocated). The
+ * right-hand sides share the sorted points and the
+ * Fourier multipliers (Sec. 3.1: the coefficients depend only on the kernel).
  */
 int addker_matvec(addker_plan* plan, const float* v, float* Kv, int nrhs);
 

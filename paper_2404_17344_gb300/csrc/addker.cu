@@ -15,6 +15,7 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -61,6 +62,10 @@ void release(Plan& p)
 {
     for (void* a : p.allocations) cudaFree(a);
     p.allocations.clear();
+    for (void* a : p.slot_allocs) cudaFree(a);
+    p.slot_allocs.clear();
+    p.slots = 0;
+    p.slot_bytes = 0;
     p.bytes = 0;
 }
 
@@ -227,10 +232,12 @@ __global__ void k_twiddles(float2* __restrict__ tf, float2* __restrict__ ti, int
 // out[i] = scale sum_s ks[s N + i]; four consecutive i per thread (16-byte accesses when vec: N % 4 == 0
 // and out 16-byte aligned)
 __global__ void k_window_sum(const float* __restrict__ ks, int P, int64_t N, float scale, float* __restrict__ out,
-                             int vec)
+                             int64_t ld, int vec)
 {
     const int64_t i0 = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
     if (i0 >= N) return;
+    ks += blockIdx.y * (int64_t)P * N;                         // right-hand side blockIdx.y
+    out += blockIdx.y * ld;
     if (vec) {
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int s = 0; s < P; ++s) {
@@ -528,7 +535,7 @@ int upload_scales(Plan& p)
     return ADDKER_OK;
 }
 
-int setup_window(Plan& p, int s, const float* X, int* keys, int* flag, std::vector<int4>& fast, std::vector<int4>& gen)
+int setup_window(Plan& p, int s, const float* X, int* keys, int* flag, std::vector<int4>* lists)
 {
     WinDev& w = p.win[s];
     const int D = w.D, n = w.n;
@@ -578,8 +585,7 @@ int setup_window(Plan& p, int s, const float* X, int* keys, int* flag, std::vect
     }
     std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) { return a.y > b.y; });
     p.n_cells[s] = ncell;
-    bool is_fast = (D == 3 && w.m == 4);
-    std::vector<int4>& dst = is_fast ? fast : gen;
+    std::vector<int4>& dst = lists[p.kind[s]];
     dst.insert(dst.end(), items.begin(), items.end());
     // scatter
     CK(cudaMemcpy(hist, off.data(), sizeof(int) * cells, cudaMemcpyHostToDevice));
@@ -603,30 +609,20 @@ int setup_window(Plan& p, int s, const float* X, int* keys, int* flag, std::vect
             w.box[t] = 1;
         }
     }
-    // buffers
+    // buffers that do not depend on the right-hand side (grids: ensure_slots)
     const int M = w.M;
-    int64_t gsz = (int64_t)w.box[0] * w.box[1] * w.box[2];
     int64_t md = 1;
     for (int t = 0; t < D; ++t) md *= M;
-    float* grid;
-    float2* hh;
-    float4 *b1 = nullptr, *b2 = nullptr, *spec;
+    float4* spec;
     float* mult;
-    CS(dalloc(p, &grid, gsz));
-    CK(cudaMemset(grid, 0, sizeof(float) * gsz));
-    CS(dalloc(p, &hh, gsz));
-    if (D == 3) {
-        CS(dalloc(p, &b1, (int64_t)w.box[0] * std::max(w.box[1], M) * M));
-        CS(dalloc(p, &b2, (int64_t)w.box[0] * M * M));
-    } else if (D == 2) {
-        CS(dalloc(p, &b1, (int64_t)w.box[0] * M));
-    }
+    w.gsz = (int64_t)w.box[0] * w.box[1] * w.box[2];
+    w.b1sz = D == 3 ? (int64_t)w.box[0] * std::max(w.box[1], M) * M : 0;
+    w.b2sz = D == 3 ? (int64_t)w.box[0] * M * M : 0;
+    w.grid = nullptr;
+    w.h = nullptr;
+    w.buf1 = w.buf2 = nullptr;
     CS(dalloc(p, &spec, md));
     CS(dalloc(p, &mult, 3 * md));
-    w.grid = grid;
-    w.h = hh;
-    w.buf1 = b1;
-    w.buf2 = b2;
     w.spec = spec;
     w.bK = mult;
     w.bD = mult + md;
@@ -689,79 +685,143 @@ struct Stage {                            // brackets one stage of a product wit
     }
 };
 
-int vec_ok(const Plan& p, const float* out)
+int vec_ok(const Plan& p, const float* out, int64_t ld)
 {
-    return (p.N % 4 == 0) && (reinterpret_cast<uintptr_t>(out) % 16 == 0);
+    return (p.N % 4 == 0) && (ld % 4 == 0) && (reinterpret_cast<uintptr_t>(out) % 16 == 0);
 }
 
-// One product for one right-hand side.
-//   mode 0: Kv = K v (if Kv) and dK[s] = dK/d ell_s v for all s (if dK; stride N)
-//   mode 1: dK = dK/d ell_s v for the single window `window`
-//   mode 2: Kv = sum_s dK/d ell_s v (shared length scale)
-int product_one(Plan& p, const float* v, float* Kv, float* dK, int window, int mode)
+// Per-window grids for `want` right-hand sides at once (grid, h and the D = 3 transform buffers, one
+// slot per right-hand side) and the window-sum scratch ks (slots x P x N). Grown on demand: the old
+// buffers are freed after the stream has drained, the grids of the new ones are zeroed, and the
+// device descriptors are re-uploaded.
+int ensure_slots(Plan& p, int want)
+{
+    want = std::min(std::max(want, 1), kMaxRhsChunk);
+    if (want <= p.slots) return ADDKER_OK;
+    int r = 1;
+    while (r < want) r *= 2;
+    r = std::min(r, kMaxRhsChunk);
+    CK(cudaStreamSynchronize(p.stream));
+    for (void* a : p.slot_allocs) cudaFree(a);
+    p.slot_allocs.clear();
+    p.bytes -= p.slot_bytes;
+    p.slot_bytes = 0;
+    p.slots = 0;
+    auto take = [&](auto** ptr, int64_t count) -> int {
+        using T = std::remove_pointer_t<std::remove_reference_t<decltype(*ptr)>>;
+        void* raw = nullptr;
+        if (count == 0) { *ptr = nullptr; return ADDKER_OK; }
+        if (cudaMalloc(&raw, sizeof(T) * (size_t)count) != cudaSuccess) { cudaGetLastError(); return ADDKER_ENOMEM; }
+        p.slot_allocs.push_back(raw);
+        p.slot_bytes += (int64_t)(sizeof(T) * (size_t)count);
+        p.bytes += (int64_t)(sizeof(T) * (size_t)count);
+        *ptr = static_cast<T*>(raw);
+        return ADDKER_OK;
+    };
+    for (int s = 0; s < p.P; ++s) {
+        WinDev& w = p.win[s];
+        float* grid;
+        float2* hh;
+        float4 *b1, *b2;
+        CS(take(&grid, r * w.gsz));
+        CS(take(&hh, r * w.gsz));
+        CS(take(&b1, r * w.b1sz));
+        CS(take(&b2, r * w.b2sz));
+        CK(cudaMemsetAsync(grid, 0, sizeof(float) * (size_t)(r * w.gsz), p.stream));
+        w.grid = grid;
+        w.h = hh;
+        w.buf1 = b1;
+        w.buf2 = b2;
+    }
+    float* ks = nullptr;
+    if (p.P > 1) CS(take(&ks, (int64_t)r * p.P * p.N));
+    p.ks = ks;
+    CK(cudaMemcpyAsync(p.wins_dev, p.win.data(), sizeof(WinDev) * p.P, cudaMemcpyHostToDevice, p.stream));
+    CK(cudaStreamSynchronize(p.stream));
+    p.slots = r;
+    return ADDKER_OK;
+}
+
+// Sum of the per-window outputs ks (R x P x N, right-hand side r at r P N) into out + r ld, scaled.
+void window_sum(Plan& p, int R, float scale, float* out, int64_t ld, cudaStream_t st)
+{
+    const dim3 grid(grid_blocks((p.N + 3) / 4, 256), R);
+    k_window_sum<<<grid, 256, 0, st>>>(p.ks, p.P, p.N, scale, out, ld, vec_ok(p, out, ld));
+}
+
+// One product for R <= slots right-hand sides v + r ldv (r < R), every stage one launch per kernel kind.
+//   mode 0: Kv + r ldk = K v_r (if Kv) and dK + r ldd + s N = dK/d ell_s v_r for all s (if dK)
+//   mode 1: dK + r ldd = dK/d ell_s v_r for the single window `window`
+//   mode 2: Kv + r ldk = sum_s dK/d ell_s v_r (shared length scale)
+int product(Plan& p, const float* v, int64_t ldv, int R, float* Kv, int64_t ldk, float* dK, int64_t ldd, int window,
+            int mode)
 {
     cudaStream_t st = p.stream;
     const int only = mode == 1 ? window : -1;
     {
-        // d = 3 grids are zeroed by the forward transform that consumes them (and at setup); the
-        // generic d < 3 path clears here
-        Stage sg(p, 0);
-        for (int s = 0; s < p.P; ++s) {
-            if (only >= 0 && s != only) continue;
-            const WinDev& w = p.win[s];
-            if (w.D == 3) continue;
-            CK(cudaMemsetAsync(w.grid, 0, sizeof(float) * (size_t)w.box[0] * w.box[1] * w.box[2], st));
-        }
-        sg.done(0);
-    }
-    {
+        // d = 3 grids are zeroed by the forward transform that consumes them, d < 3 grids by the small
+        // transform, and every grid at allocation, so nothing is cleared here
         Stage sg(p, 1);
         int n = 0;
-        CK(launch_spread(p, only, v, st, &n));
+        CK(launch_spread(p, only, v, ldv, R, st, &n));
         sg.done(n);
     }
     {
         Stage sg(p, 2);
         int n = 0;
-        CK(launch_transforms(p, only, st, &n, false));
+        CK(launch_transforms(p, only, R, st, &n, false));
         sg.done(n);
     }
     const float* ones = p.scale_dev;
     const float* sf2 = p.scale_dev + p.P;
     const float* sder = p.scale_dev + 2 * p.P;
+    const int64_t PN = (int64_t)p.P * p.N;
     int n = 0;
     Stage sg(p, 3);
     if (mode == 1) {                               // window s only, written at offset 0
-        CK(launch_gather(p, only, nullptr, 0, dK, 0, ones, sder, st, &n));
+        CK(launch_gather(p, only, nullptr, 0, 0, dK, 0, ldd, R, ones, sder, st, &n));
         sg.done(n);
         return ADDKER_OK;
     }
     if (mode == 2) {
         if (p.P == 1) {
-            CK(launch_gather(p, -1, nullptr, 0, Kv, 0, ones, sder, st, &n));
+            CK(launch_gather(p, -1, nullptr, 0, 0, Kv, 0, ldk, R, ones, sder, st, &n));
             sg.done(n);
             return ADDKER_OK;
         }
-        CK(launch_gather(p, -1, nullptr, 0, p.ks, p.N, ones, sder, st, &n));
+        CK(launch_gather(p, -1, nullptr, 0, 0, p.ks, p.N, PN, R, ones, sder, st, &n));
         sg.done(n);
         Stage sum(p, 4);
-        k_window_sum<<<grid_blocks((p.N + 3) / 4, 256), 256, 0, st>>>(p.ks, p.P, p.N, 1.0f, Kv, vec_ok(p, Kv));
+        window_sum(p, R, 1.0f, Kv, ldk, st);
         CK(cudaGetLastError());
         sum.done(1);
         return ADDKER_OK;
     }
     if (p.P == 1) {
-        CK(launch_gather(p, -1, Kv, 0, dK, p.N, sf2, sder, st, &n));
+        CK(launch_gather(p, -1, Kv, 0, ldk, dK, p.N, ldd, R, sf2, sder, st, &n));
         sg.done(n);
         return ADDKER_OK;
     }
-    CK(launch_gather(p, -1, p.ks, p.N, dK, p.N, ones, sder, st, &n));
+    CK(launch_gather(p, -1, p.ks, p.N, PN, dK, p.N, ldd, R, ones, sder, st, &n));
     sg.done(n);
     Stage sum(p, 4);
-    k_window_sum<<<grid_blocks((p.N + 3) / 4, 256), 256, 0, st>>>(p.ks, p.P, p.N, (float)(p.sigma_f * p.sigma_f), Kv,
-                                                                   vec_ok(p, Kv));
+    window_sum(p, R, (float)(p.sigma_f * p.sigma_f), Kv, ldk, st);
     CK(cudaGetLastError());
     sum.done(1);
+    return ADDKER_OK;
+}
+
+// nrhs right-hand sides (columns of length N, v + j N) in chunks of at most kMaxRhsChunk.
+int product_all(Plan& p, const float* v, int nrhs, float* Kv, float* dK, int window, int mode)
+{
+    // a batch that cannot get more slots runs in single-right-hand-side chunks
+    if (ensure_slots(p, nrhs) != ADDKER_OK) CS(ensure_slots(p, 1));
+    const int64_t N = p.N;
+    const int64_t ldd = mode == 0 ? N * p.P : N;
+    for (int j = 0; j < nrhs; j += p.slots) {
+        const int R = std::min(p.slots, nrhs - j);
+        CS(product(p, v + j * N, N, R, Kv ? Kv + j * N : nullptr, N, dK ? dK + j * ldd : nullptr, ldd, window, mode));
+    }
     return ADDKER_OK;
 }
 
@@ -910,6 +970,7 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
     p.bandwidth.assign(bandwidth, bandwidth + P);
     p.win.resize(P);
     p.dims.resize(P);
+    p.kind.resize(P);
     p.n_cells.assign(P, 0);
     double b_shape = M_PI * (2.0 - 1.0 / o.sigma_os);
     for (int s = 0; s < P; ++s) {
@@ -917,6 +978,7 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
         std::memset(&w, 0, sizeof(w));
         w.D = win_off[s + 1] - win_off[s];
         p.dims[s] = w.D;
+        p.kind[s] = kind_of(w.D, cutoff);
         w.M = bandwidth[s];
         w.n = (int)std::lround(o.sigma_os * w.M);
         w.m = cutoff;
@@ -926,38 +988,39 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
     int* keys = nullptr;
     int* flag = nullptr;
     int status = ADDKER_OK;
-    std::vector<int4> fast, gen;
-    p.item_begin_fast.assign(1, 0);
-    p.item_begin_gen.assign(1, 0);
+    std::vector<int4> lists[kKinds];
+    for (int k = 0; k < kKinds; ++k) p.item_begin[k].assign(1, 0);
     if (cudaMalloc(&keys, sizeof(int) * (size_t)(N + 1)) != cudaSuccess) status = ADDKER_ENOMEM;
     if (status == ADDKER_OK) {
         flag = keys + N;
         if (cudaMemset(flag, 0, sizeof(int)) != cudaSuccess) status = ADDKER_ECUDA;
     }
     for (int s = 0; s < P && status == ADDKER_OK; ++s) {
-        status = setup_window(p, s, points, keys, flag, fast, gen);
-        p.item_begin_fast.push_back((int)fast.size());
-        p.item_begin_gen.push_back((int)gen.size());
+        status = setup_window(p, s, points, keys, flag, lists);
+        for (int k = 0; k < kKinds; ++k) p.item_begin[k].push_back((int)lists[k].size());
     }
     if (keys) cudaFree(keys);
     if (status == ADDKER_OK) {
-        status = dalloc(p, &p.items_fast, (int64_t)fast.size());
-        if (status == ADDKER_OK) status = dalloc(p, &p.items_gen, (int64_t)gen.size());
-        if (status == ADDKER_OK && !fast.empty() &&
-            cudaMemcpy(p.items_fast, fast.data(), sizeof(int4) * fast.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-            status = ADDKER_ECUDA;
-        if (status == ADDKER_OK && !gen.empty() &&
-            cudaMemcpy(p.items_gen, gen.data(), sizeof(int4) * gen.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        // one device array, the kinds one after another; item_begin becomes absolute
+        std::vector<int4> all;
+        for (int k = 0; k < kKinds; ++k) {
+            const int base = (int)all.size();
+            for (int& b : p.item_begin[k]) b += base;
+            all.insert(all.end(), lists[k].begin(), lists[k].end());
+        }
+        status = dalloc(p, &p.items, std::max<int64_t>(1, (int64_t)all.size()));
+        if (status == ADDKER_OK && !all.empty() &&
+            cudaMemcpy(p.items, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             status = ADDKER_ECUDA;
     }
     if (status == ADDKER_OK) status = dalloc(p, &p.wins_dev, P);
-    if (status == ADDKER_OK && P > 1) status = dalloc(p, &p.ks, (int64_t)P * N);
     if (status == ADDKER_OK) status = dalloc(p, &p.scale_dev, 3 * P);
     if (status == ADDKER_OK) status = dalloc(p, &p.dots, 2 * P);
     for (int s = 0; s < P && status == ADDKER_OK; ++s) status = compute_multipliers(p, s);
     if (status == ADDKER_OK && cudaMemcpy(p.wins_dev, p.win.data(), sizeof(WinDev) * P, cudaMemcpyHostToDevice) != cudaSuccess)
         status = ADDKER_ECUDA;
     if (status == ADDKER_OK) status = upload_scales(p);
+    if (status == ADDKER_OK) status = ensure_slots(p, 1);
     if (status == ADDKER_OK && cudaDeviceSynchronize() != cudaSuccess) status = ADDKER_ECUDA;
     if (status != ADDKER_OK) {
         cudaGetLastError();
@@ -993,11 +1056,7 @@ int addker_set_stream(addker_plan* plan, void* stream)
 int addker_matvec_all(addker_plan* plan, const float* v, float* Kv, float* dKdell, int nrhs)
 {
     if (!plan || !v || !Kv || nrhs < 1) return ADDKER_EINVAL;
-    Plan& p = plan->p;
-    for (int j = 0; j < nrhs; ++j)
-        CS(product_one(p, v + (int64_t)j * p.N, Kv + (int64_t)j * p.N,
-                       dKdell ? dKdell + (int64_t)j * p.N * p.P : nullptr, -1, 0));
-    return ADDKER_OK;
+    return product_all(plan->p, v, nrhs, Kv, dKdell, -1, 0);
 }
 
 int addker_matvec(addker_plan* plan, const float* v, float* Kv, int nrhs)
@@ -1010,19 +1069,12 @@ int addker_dmatvec(addker_plan* plan, int param, const float* v, float* out, int
     if (!plan || !v || !out || nrhs < 1) return ADDKER_EINVAL;
     Plan& p = plan->p;
     if (param >= p.P || param < ADDKER_SIGMA_F) return ADDKER_EINVAL;
-    for (int j = 0; j < nrhs; ++j) {
-        const float* vj = v + (int64_t)j * p.N;
-        float* oj = out + (int64_t)j * p.N;
-        if (param >= 0) {
-            CS(product_one(p, vj, nullptr, oj, param, 1));
-        } else if (param == ADDKER_SIGMA_F) {
-            CS(product_one(p, vj, oj, nullptr, -1, 0));
-            k_scale<<<grid_blocks(p.N, 256), 256, 0, p.stream>>>(oj, p.N, (float)(2.0 / p.sigma_f), oj);
-            CK(cudaGetLastError());
-        } else {
-            CS(product_one(p, vj, oj, nullptr, -1, 2));
-        }
-    }
+    if (param >= 0) return product_all(p, v, nrhs, nullptr, out, param, 1);
+    if (param == ADDKER_ELL_SHARED) return product_all(p, v, nrhs, out, nullptr, -1, 2);
+    CS(product_all(p, v, nrhs, out, nullptr, -1, 0));
+    const int64_t len = p.N * (int64_t)nrhs;
+    k_scale<<<grid_blocks(len, 256), 256, 0, p.stream>>>(out, len, (float)(2.0 / p.sigma_f), out);
+    CK(cudaGetLastError());
     return ADDKER_OK;
 }
 
@@ -1031,6 +1083,7 @@ int addker_vjp(addker_plan* plan, const float* v, const float* w, float* grad_v,
 {
     if (!plan || !v || !w || !grad_v || !grad_theta || !grad_points) return ADDKER_EINVAL;
     Plan& p = plan->p;
+    CS(ensure_slots(p, 1));
     cudaStream_t st = p.stream;
     float* gx = grad_points;
     CK(cudaMemsetAsync(gx, 0, sizeof(float) * (size_t)p.N * p.d, st));
@@ -1039,18 +1092,12 @@ int addker_vjp(addker_plan* plan, const float* v, const float* w, float* grad_v,
     float* ks = p.P > 1 ? p.ks : grad_v;
     for (int pass = 0; pass < 2; ++pass) {
         const float* u = pass == 0 ? w : v;
-        for (int s = 0; s < p.P; ++s) {
-            const WinDev& wd = p.win[s];
-            if (wd.D != 3) CK(cudaMemsetAsync(wd.grid, 0, sizeof(float) * (size_t)wd.box[0] * wd.box[1] * wd.box[2], st));
-        }
-        CK(launch_spread(p, -1, u, st, nullptr));
-        CK(launch_transforms(p, -1, st, nullptr, false));
+        CK(launch_spread(p, -1, u, p.N, 1, st, nullptr));         // slot 0; the transforms re-zero the grids
+        CK(launch_transforms(p, -1, 1, st, nullptr, false));
         CK(launch_gather_grad(p, pass, pass == 0 ? v : w, ks, gx, st, nullptr));
         if (pass == 0) {
             if (p.P > 1)
-                k_window_sum<<<grid_blocks((p.N + 3) / 4, 256), 256, 0, st>>>(p.ks, p.P, p.N,
-                                                                               (float)(p.sigma_f * p.sigma_f), grad_v,
-                                                                               vec_ok(p, grad_v));
+                window_sum(p, 1, (float)(p.sigma_f * p.sigma_f), grad_v, p.N, st);
             else
                 k_scale<<<grid_blocks(p.N, 256), 256, 0, st>>>(grad_v, p.N, (float)(p.sigma_f * p.sigma_f), grad_v);
             CK(cudaGetLastError());
@@ -1177,7 +1224,7 @@ int addker_info(const addker_plan* plan, int64_t* info, int cap)
 {
     if (!plan) return ADDKER_EINVAL;
     const Plan& p = plan->p;
-    std::vector<int64_t> v = {p.N, p.P, (int64_t)(p.item_begin_fast.back() + p.item_begin_gen.back()), p.bytes};
+    std::vector<int64_t> v = {p.N, p.P, (int64_t)p.item_begin[kKinds - 1].back(), p.bytes};
     for (int s = 0; s < p.P; ++s) {
         v.push_back(p.win[s].D);
         v.push_back(p.win[s].M);
@@ -1197,10 +1244,11 @@ int addker_debug_stage(addker_plan* plan, int window, int stage, const float* v,
     int64_t full = 1, md = 1;
     for (int t = 0; t < w.D; ++t) { full *= w.n; md *= w.M; }
     if ((stage == 0 && cap < full) || (stage == 1 && cap < 2 * md)) return ADDKER_EINVAL;
+    CS(ensure_slots(p, 1));
     cudaStream_t st = p.stream;
     int64_t gsz = (int64_t)w.box[0] * w.box[1] * w.box[2];
     CK(cudaMemsetAsync(w.grid, 0, sizeof(float) * gsz, st));
-    CK(launch_spread(p, window, v, st));
+    CK(launch_spread(p, window, v, p.N, 1, st));                     // slot 0
     if (stage == 0) {
         std::vector<float> g(gsz);
         CK(cudaMemcpyAsync(g.data(), w.grid, sizeof(float) * gsz, cudaMemcpyDeviceToHost, st));
@@ -1221,8 +1269,7 @@ int addker_debug_stage(addker_plan* plan, int window, int stage, const float* v,
         }
         return ADDKER_OK;
     }
-    CK(launch_transforms(p, window, st, nullptr, true));
-    CK(cudaMemsetAsync(w.grid, 0, sizeof(float) * gsz, st));            // d < 3 passes do not consume it
+    CK(launch_transforms(p, window, 1, st, nullptr, true));           // consumes (re-zeroes) the grid
     std::vector<float4> s(md);
     CK(cudaMemcpyAsync(s.data(), w.spec, sizeof(float4) * md, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

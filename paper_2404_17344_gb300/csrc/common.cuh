@@ -24,6 +24,10 @@
 namespace addker {
 
 constexpr int kMaxWindows = 64;
+constexpr int kMaxRhsChunk = 8;         // right-hand sides processed together by one launch per stage
+// kernel kinds of the item lists: m = 4 fast kernels for D = 3, 1, 2, then the generic ones for D = 1, 2, 3
+enum { kKindFast3 = 0, kKindLow1 = 1, kKindLow2 = 2, kKindGen1 = 3, kKindGen2 = 4, kKindGen3 = 5, kKinds = 6 };
+inline int kind_of(int D, int m) { return m == 4 ? (D == 3 ? kKindFast3 : D) : 2 + D; }
 constexpr int kItemPoints = 256;        // points per work item (one warp)
 constexpr int kMaxBandwidth = 64;
 
@@ -53,6 +57,9 @@ struct WinDev {                          // copied by value into kernel paramete
     const float* bK;
     const float* bD;
     const float* dconv;                  // 1 / (n^D prod_t phi_hat(k_t)): the adjoint NFFT's deconvolution
+    // per right-hand-side slots: slot r of grid and h starts at + r*gsz, of buf1 at + r*b1sz, of
+    // buf2 at + r*b2sz (elements of the respective type)
+    int64_t gsz, b1sz, b2sz;
     const float2* twf[3];                // [axis]: box[axis] x M
     const float2* twi[3];                // [axis]: M x box[axis]
     int D, M, n, m;
@@ -73,14 +80,17 @@ struct Plan {
     std::vector<WinDev> win;              // host copies of the per-window descriptors
     WinDev* wins_dev = nullptr;           // device copy of `win`
     std::vector<int> n_cells;             // non-empty cells per window
-    // items: fast 3-D kernels (D = 3, m = 4) and generic kernels, grouped by window; items of
-    // window s are [begin[s], begin[s+1]) of the respective list
-    int4* items_fast = nullptr;
-    int4* items_gen = nullptr;
-    std::vector<int> item_begin_fast, item_begin_gen;
+    // work items of all windows in one device array, grouped by kernel kind and, within a kind, by
+    // window: items of window s are [item_begin[k][s], item_begin[k][s+1]) for its kind k = kind[s]
+    int4* items = nullptr;
+    std::vector<int> item_begin[kKinds];
+    std::vector<int> kind;
+    int slots = 0;                        // right-hand-side slots allocated per window
+    std::vector<void*> slot_allocs;       // grid, h, buf1, buf2 of all slots (re-made when slots grow)
+    int64_t slot_bytes = 0;
     WinPoly poly;                         // window polynomials for cutoff m and shape b
     float* scale_dev = nullptr;           // 3P floats: [0,P) ones, [P,2P) sigma_f^2, [2P,3P) sigma_f^2 2/ell_s
-    float* ks = nullptr;                  // P x N per-window K_s v, scratch for the window sum
+    float* ks = nullptr;                  // slots x P x N per-window K_s v, scratch for the window sum
     float* stage_v = nullptr;             // host-API staging (N x nrhs), allocated on demand
     float* stage_k = nullptr;
     float* stage_d = nullptr;
@@ -164,13 +174,16 @@ __device__ __forceinline__ void window_weights_grad_n(const WinPoly& P, float x,
 }
 
 // ---- launchers implemented in the other translation units -------------------------
-// Each launcher returns the number of kernels it launched through *count (may be NULL).
-cudaError_t launch_spread(const Plan& p, int window_or_all, const float* v, cudaStream_t st, int* count = nullptr);
-// Outputs of window s for the point with original index i go to outK[i + s*strideK] and
-// outD[i + s*strideD] (either may be NULL), scaled by scaleK[s] and scaleD[s] (device arrays).
-cudaError_t launch_gather(const Plan& p, int window_or_all, float* outK, int64_t strideK, float* outD,
-                          int64_t strideD, const float* scaleK, const float* scaleD, cudaStream_t st,
+// Each launcher returns the number of kernels it launched through *count (may be NULL). All of them
+// process nrhs (<= kMaxRhsChunk) right-hand sides: rhs r reads v + r*ldv and uses slot r of the grids.
+cudaError_t launch_spread(const Plan& p, int window_or_all, const float* v, int64_t ldv, int nrhs, cudaStream_t st,
                           int* count = nullptr);
+// Outputs of window s for rhs r and the point with original index i go to
+// outK[i + s*strideK + r*rstrideK] and outD[i + s*strideD + r*rstrideD] (either may be NULL), scaled by
+// scaleK[s] and scaleD[s] (device arrays).
+cudaError_t launch_gather(const Plan& p, int window_or_all, float* outK, int64_t strideK, int64_t rstrideK,
+                          float* outD, int64_t strideD, int64_t rstrideD, int nrhs, const float* scaleK,
+                          const float* scaleD, cudaStream_t st, int* count = nullptr);
 // Gradient gathers of addker_vjp (gradients.cu). Pass 0 reads the grids of w: writes f^K to
 // ks[s N + i], accumulates dots[s] += v_i f^K, dots[P + s] += v_i f^D and
 // grad_x[i d + feat] += sigma_f^2 v_i grad f^K. Pass 1 reads the grids of v and accumulates
@@ -185,8 +198,8 @@ int multipliers_with_scratch(const WinDev& w, double ell, int p_opt, double eps_
 cudaError_t twiddles_into(const WinDev& w, float2* const tw[3], cudaStream_t st);
 cudaError_t launch_transforms_window(const WinDev& w, const WinDev* w_dev, cudaStream_t st);
 
-// grid -> (multiply) -> h for one window or all (window < 0). spec_only: stop after the forward
-// transform and write S_k = G_k dconv_k (the adjoint NFFT) to each window's spec.
-cudaError_t launch_transforms(const Plan& p, int window_or_all, cudaStream_t st, int* count, bool spec_only);
+// grid -> (multiply) -> h for one window or all (window < 0) and nrhs slots. spec_only: stop after
+// the forward transform and write S_k = G_k dconv_k (the adjoint NFFT) to slot 0's spec.
+cudaError_t launch_transforms(const Plan& p, int window_or_all, int nrhs, cudaStream_t st, int* count, bool spec_only);
 
 }  // namespace addker

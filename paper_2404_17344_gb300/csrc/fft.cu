@@ -13,15 +13,14 @@
 //   k_xround   per column:   t[x][c] -> S[kx][c] -> B[x][c]      (x forward, multiply, x inverse)
 //   k_inv_yz   per x-slab:   B[x][ky][kz] -> h[x][y][z]          (y then z inverse, real part)
 // The x round trip fuses forward DFT, multiplication and inverse DFT because all three act on the
-// same column (ky, kz). D = 1, 2 use the generic one-axis pass k_dft_pass per window.
+// same column (ky, kz). D = 1, 2 use k_small_transform: one block per window does every pass.
+// Each right-hand side has its own slot in every buffer (blockIdx.z, or blockIdx.y for the small
+// kernel), so one launch transforms up to kMaxRhsChunk right-hand sides of all windows.
 #include "common.cuh"
 
 namespace addker {
 
 namespace {
-
-enum { IN_REAL = 0, IN_CPLX = 1, IN_PAIR = 2 };
-enum { OUT_CPLX = 1, OUT_PAIR = 2, OUT_MUL = 3, OUT_REAL_PAIR = 4 };
 
 __device__ __forceinline__ float2 cmad(float2 a, float2 b, float2 c)      // c + a*b
 {
@@ -53,7 +52,8 @@ __global__ void __launch_bounds__(kT) k_fwd_yz(const WinDev* __restrict__ wins, 
     float2* ty = tz + b2 * M;
     float2* t1 = ty + b1 * M;
     float* gs = reinterpret_cast<float*>(t1 + b1 * M);
-    float* g = W.grid + (size_t)x * b1 * b2;
+    const int r = blockIdx.z;                                  // right-hand-side slot
+    float* g = W.grid + r * W.gsz + (size_t)x * b1 * b2;
     for (int i = threadIdx.x; i < b1 * b2; i += kT) {
         gs[i] = g[i];
         g[i] = 0.f;                      // the slab is consumed: leave the grid zeroed for the next spread
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kT) k_fwd_yz(const WinDev* __restrict__ wins, 
     }
     __syncthreads();
     // phase 2: rows ky, columns kz (2x2 blocks)
-    float2* out = reinterpret_cast<float2*>(W.buf1) + (size_t)x * M * M;
+    float2* out = reinterpret_cast<float2*>(W.buf1 + r * W.b1sz) + (size_t)x * M * M;
     for (int o = threadIdx.x; o < Mh * Mh; o += kT) {
         const int ky = 2 * (o / Mh), kz = 2 * (o % Mh);
         float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
@@ -120,7 +120,8 @@ __global__ void __launch_bounds__(kT) k_xround(const WinDev* __restrict__ wins, 
     float2* ts = tx + b0 * M;
     float4* ss = reinterpret_cast<float4*>(ts + b0 * 32);
     const int cols = min(32, MM - c0);                          // M^2 need not be a multiple of 32
-    const float2* t = reinterpret_cast<const float2*>(W.buf1);
+    const int r = blockIdx.z;                                  // right-hand-side slot
+    const float2* t = reinterpret_cast<const float2*>(W.buf1 + r * W.b1sz);
     for (int i = threadIdx.x; i < b0 * 32; i += kT)
         ts[i] = (i & 31) < cols ? t[(size_t)(i >> 5) * MM + c0 + (i & 31)] : make_float2(0.f, 0.f);
     for (int i = threadIdx.x; i < b0 * M; i += kT) tx[i] = W.twf[0][i];
@@ -144,18 +145,18 @@ __global__ void __launch_bounds__(kT) k_xround(const WinDev* __restrict__ wins, 
         }
         const float2 acc[2][2] = {{a00, a01}, {a10, a11}};
 #pragma unroll
-        for (int r = 0; r < 2; ++r)
+        for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 if (j + q >= cols) {
-                    if (!spec_only) ss[(kx + r) * 32 + j + q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (!spec_only) ss[(kx + rr) * 32 + j + q] = make_float4(0.f, 0.f, 0.f, 0.f);
                     continue;
                 }
-                const size_t k = (size_t)(kx + r) * MM + c0 + j + q;
+                const size_t k = (size_t)(kx + rr) * MM + c0 + j + q;
                 const float a = __ldg(mK + k), d = __ldg(mD + k);
-                const float4 v = make_float4(a * acc[r][q].x, a * acc[r][q].y, d * acc[r][q].x, d * acc[r][q].y);
+                const float4 v = make_float4(a * acc[rr][q].x, a * acc[rr][q].y, d * acc[rr][q].x, d * acc[rr][q].y);
                 if (spec_only) W.spec[k] = v;
-                else ss[(kx + r) * 32 + j + q] = v;
+                else ss[(kx + rr) * 32 + j + q] = v;
             }
     }
     if (spec_only) return;
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(kT) k_xround(const WinDev* __restrict__ wins, 
             d11 = cmadc(make_float2(s1.z, s1.w), w1, d11);
         }
         if (j >= cols) continue;
-        float4* B = W.buf2 + c0 + j;
+        float4* B = W.buf2 + r * W.b2sz + c0 + j;
         const bool q1 = j + 1 < cols;
         B[(size_t)x0 * MM] = make_float4(k00.x, k00.y, d00.x, d00.y);
         if (q1) B[(size_t)x0 * MM + 1] = make_float4(k01.x, k01.y, d01.x, d01.y);
@@ -205,7 +206,8 @@ __global__ void __launch_bounds__(kT) k_inv_yz(const WinDev* __restrict__ wins, 
     float4* b1s = bs + MM;
     float2* ty = reinterpret_cast<float2*>(b1s + b1 * M);
     float2* tz = ty + b1 * M;
-    const float4* B = W.buf2 + (size_t)x * MM;
+    const int r = blockIdx.z;                                  // right-hand-side slot
+    const float4* B = W.buf2 + r * W.b2sz + (size_t)x * MM;
     for (int i = threadIdx.x; i < MM; i += kT) bs[i] = B[i];
     for (int i = threadIdx.x; i < b1 * M; i += kT) ty[i] = W.twf[1][i];
     for (int i = threadIdx.x; i < b2 * M; i += kT) tz[i] = W.twf[2][i];
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(kT) k_inv_yz(const WinDev* __restrict__ wins, 
         }
     }
     __syncthreads();
-    float2* h = W.h + (size_t)x * b1 * b2;
+    float2* h = W.h + r * W.gsz + (size_t)x * b1 * b2;
     const int nb2 = (b2 + 1) / 2;
     for (int o = threadIdx.x; o < nb1 * nb2; o += kT) {          // 2x2 blocks (y, z)
         const int y0 = 2 * (o / nb2), y1 = min(y0 + 1, b1 - 1);
@@ -266,84 +268,130 @@ __global__ void __launch_bounds__(kT) k_inv_yz(const WinDev* __restrict__ wins, 
     }
 }
 
-// ------------------------------------------------------------------ generic one-axis pass ----
-// out[a][k][b] = sum_l in[a][l][b] tw[l][k]; one thread per output.
-template <int IN, int OUT>
-__global__ void __launch_bounds__(256) k_dft_pass(const void* __restrict__ in_, void* __restrict__ out_,
-                                                  const float2* __restrict__ tw, int A, int L, int K, int B,
-                                                  const float* __restrict__ bK, const float* __restrict__ bD)
+// ------------------------------------------------------------ D = 1, 2: one block per window ----
+// The whole transform of a small grid in one block (box <= 64^2 samples, M <= 64), every pass from
+// shared memory, one thread per output:
+//   D = 1:  G[k] = sum_x g[x] tf[x][k];  S = (bK, bD) G;  h[x] = Re sum_k S[k] conj(tf[x][k])
+//   D = 2:  t[x][ky] = sum_y g[x][y] tf1[y][ky];  G[kx][ky] = sum_x t[x][ky] tf0[x][kx];  S = (bK, bD) G;
+//           B[x][ky] = sum_kx S[kx][ky] conj(tf0[x][kx]);  h[x][y] = Re sum_ky B[x][ky] conj(tf1[y][ky])
+// The grid is zeroed once read. spec_only: write G dconv to spec and stop.
+// Bytes in front of S: the grid, t and G of the forward passes, or B of the inverse, whichever is larger
+// (16-byte multiple).
+__host__ __device__ inline size_t small_front(int b0, int b1, int M, int D)
 {
-    const int64_t total = (int64_t)A * K * B;
-    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
-         o += (int64_t)gridDim.x * blockDim.x) {
-        const int b = (int)(o % B);
-        const int k = (int)((o / B) % K);
-        const int a = (int)(o / ((int64_t)B * K));
-        const int64_t ibase = (int64_t)a * L * B + b;
-        float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
-        for (int l = 0; l < L; ++l) {
-            const float2 w = tw[l * K + k];
-            const int64_t ii = ibase + (int64_t)l * B;
-            if (IN == IN_REAL) {
-                const float g = reinterpret_cast<const float*>(in_)[ii];
-                s0.x = fmaf(g, w.x, s0.x);
-                s0.y = fmaf(g, w.y, s0.y);
-            } else if (IN == IN_CPLX) {
-                s0 = cmad(reinterpret_cast<const float2*>(in_)[ii], w, s0);
-            } else {
-                const float4 z = reinterpret_cast<const float4*>(in_)[ii];
-                s0 = cmad(make_float2(z.x, z.y), w, s0);
-                s1 = cmad(make_float2(z.z, z.w), w, s1);
+    const int MD = D == 2 ? M * M : M;
+    const size_t fwd = sizeof(float) * ((b0 * b1 + 3) & ~3) + sizeof(float2) * ((D == 2 ? b0 * M : 0) + MD + (MD & 1));
+    const size_t inv = D == 2 ? sizeof(float4) * b0 * M : 0;
+    return fwd > inv ? fwd : inv;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kT) k_small_transform(const WinDev* __restrict__ wins, int w0, int spec_only)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const WinDev& W = wins[w0 + blockIdx.x];
+    if (W.D != D) return;
+    const int r = blockIdx.y;
+    const int b0 = W.box[0], b1 = D == 2 ? W.box[1] : 1, M = W.M;
+    const int MD = D == 2 ? M * M : M;
+    float* grid = W.grid + r * W.gsz;
+    float2* h = W.h + r * W.gsz;
+    const float2* tf0 = W.twf[0];
+    const float2* tf1 = W.twf[1];
+    // gs, t and G are dead once S is written, so B reuses their space (see small_smem)
+    float* gs = reinterpret_cast<float*>(smem);                                   // b0 * b1
+    float2* t = reinterpret_cast<float2*>(smem + sizeof(float) * ((b0 * b1 + 3) & ~3));   // b0 * M (D = 2)
+    float2* G = t + (D == 2 ? b0 * M : 0);                                       // MD
+    float4* B = reinterpret_cast<float4*>(smem);                                 // b0 * M (D = 2)
+    float4* S = reinterpret_cast<float4*>(smem + small_front(b0, b1, M, D));     // MD
+    for (int i = threadIdx.x; i < b0 * b1; i += kT) {
+        gs[i] = grid[i];
+        grid[i] = 0.f;
+    }
+    __syncthreads();
+    if (D == 1) {
+        for (int k = threadIdx.x; k < M; k += kT) {
+            float2 acc = make_float2(0.f, 0.f);
+            for (int x = 0; x < b0; ++x) {
+                const float2 w = tf0[x * M + k];
+                acc.x = fmaf(gs[x], w.x, acc.x);
+                acc.y = fmaf(gs[x], w.y, acc.y);
             }
+            G[k] = acc;
         }
-        if (OUT == OUT_CPLX) {
-            reinterpret_cast<float2*>(out_)[o] = s0;
-        } else if (OUT == OUT_PAIR) {
-            reinterpret_cast<float4*>(out_)[o] = make_float4(s0.x, s0.y, s1.x, s1.y);
-        } else if (OUT == OUT_MUL) {
-            const float mk = bK[o], md = bD[o];
-            reinterpret_cast<float4*>(out_)[o] = make_float4(mk * s0.x, mk * s0.y, md * s0.x, md * s0.y);
-        } else {
-            reinterpret_cast<float2*>(out_)[o] = make_float2(s0.x, s1.x);
-        }
-    }
-}
-
-template <int IN, int OUT>
-void pass(const void* in, void* out, const float2* tw, int A, int L, int K, int B, const float* bK,
-          const float* bD, cudaStream_t st)
-{
-    int64_t total = (int64_t)A * K * B;
-    int blocks = (int)((total + 255) / 256);
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    k_dft_pass<IN, OUT><<<blocks, 256, 0, st>>>(in, out, tw, A, L, K, B, bK, bD);
-}
-
-// D = 1, 2: forward (multiply fused into the last pass) then inverse, one window
-int generic_window(const WinDev& w, cudaStream_t st, bool spec_only)
-{
-    const int M = w.M;
-    const int b0 = w.box[0], b1 = w.box[1];
-    const float* mK = spec_only ? w.dconv : w.bK;
-    const float* mD = spec_only ? w.dconv : w.bD;
-    int n = 0;
-    if (w.D == 1) {
-        pass<IN_REAL, OUT_MUL>(w.grid, w.spec, w.twf[0], 1, b0, M, 1, mK, mD, st);
-        ++n;
-        if (spec_only) return n;
-        pass<IN_PAIR, OUT_REAL_PAIR>(w.spec, w.h, w.twi[0], 1, M, b0, 1, nullptr, nullptr, st);
-        ++n;
     } else {
-        float2* t1 = reinterpret_cast<float2*>(w.buf1);
-        pass<IN_REAL, OUT_CPLX>(w.grid, t1, w.twf[1], b0, b1, M, 1, nullptr, nullptr, st);       // [x][k1]
-        pass<IN_CPLX, OUT_MUL>(t1, w.spec, w.twf[0], 1, b0, M, M, mK, mD, st);                  // [k0][k1]
-        n += 2;
-        if (spec_only) return n;
-        pass<IN_PAIR, OUT_PAIR>(w.spec, w.buf1, w.twi[0], 1, M, b0, M, nullptr, nullptr, st);         // [x][k1]
-        pass<IN_PAIR, OUT_REAL_PAIR>(w.buf1, w.h, w.twi[1], b0, M, b1, 1, nullptr, nullptr, st);     // [x][y]
-        n += 2;
+        for (int o = threadIdx.x; o < b0 * M; o += kT) {
+            const int x = o / M, ky = o % M;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int y = 0; y < b1; ++y) {
+                const float2 w = tf1[y * M + ky];
+                acc.x = fmaf(gs[x * b1 + y], w.x, acc.x);
+                acc.y = fmaf(gs[x * b1 + y], w.y, acc.y);
+            }
+            t[o] = acc;
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < MD; o += kT) {
+            const int kx = o / M, ky = o % M;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int x = 0; x < b0; ++x) acc = cmad(t[x * M + ky], tf0[x * M + kx], acc);
+            G[o] = acc;
+        }
     }
-    return n;
+    __syncthreads();
+    const float* mK = spec_only ? W.dconv : W.bK;
+    const float* mD = spec_only ? W.dconv : W.bD;
+    for (int o = threadIdx.x; o < MD; o += kT) {
+        const float a = mK[o], d = mD[o];
+        const float4 v = make_float4(a * G[o].x, a * G[o].y, d * G[o].x, d * G[o].y);
+        if (spec_only) W.spec[o] = v;
+        else S[o] = v;
+    }
+    if (spec_only) return;
+    __syncthreads();
+    if (D == 1) {
+        for (int x = threadIdx.x; x < b0; x += kT) {
+            float hK = 0.f, hD = 0.f;
+            for (int k = 0; k < M; ++k) {
+                const float4 v = S[k];
+                const float2 w = tf0[x * M + k];
+                hK = fmaf(v.x, w.x, fmaf(v.y, w.y, hK));      // Re(s conj(w))
+                hD = fmaf(v.z, w.x, fmaf(v.w, w.y, hD));
+            }
+            h[x] = make_float2(hK, hD);
+        }
+    } else {
+        for (int o = threadIdx.x; o < b0 * M; o += kT) {
+            const int x = o / M, ky = o % M;
+            float2 aK = make_float2(0.f, 0.f), aD = make_float2(0.f, 0.f);
+            for (int kx = 0; kx < M; ++kx) {
+                const float4 v = S[kx * M + ky];
+                const float2 w = tf0[x * M + kx];
+                aK = cmadc(make_float2(v.x, v.y), w, aK);
+                aD = cmadc(make_float2(v.z, v.w), w, aD);
+            }
+            B[o] = make_float4(aK.x, aK.y, aD.x, aD.y);
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < b0 * b1; o += kT) {
+            const int x = o / b1, y = o % b1;
+            float hK = 0.f, hD = 0.f;
+            for (int ky = 0; ky < M; ++ky) {
+                const float4 v = B[x * M + ky];
+                const float2 w = tf1[y * M + ky];
+                hK = fmaf(v.x, w.x, fmaf(v.y, w.y, hK));
+                hD = fmaf(v.z, w.x, fmaf(v.w, w.y, hD));
+            }
+            h[o] = make_float2(hK, hD);
+        }
+    }
+}
+
+size_t small_smem(const WinDev& w)
+{
+    const int b0 = w.box[0], b1 = w.D == 2 ? w.box[1] : 1, M = w.M;
+    const int MD = w.D == 2 ? M * M : M;
+    return small_front(b0, b1, M, w.D) + sizeof(float4) * MD;
 }
 
 }  // namespace
@@ -375,19 +423,22 @@ static void ensure_attrs()
     cudaFuncSetAttribute(k_fwd_yz, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_xround, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_inv_yz, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_small_transform<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_small_transform<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     fused_attrs_set = true;
 }
 
-cudaError_t launch_transforms(const Plan& p, int window, cudaStream_t st, int* count, bool spec_only)
+cudaError_t launch_transforms(const Plan& p, int window, int nrhs, cudaStream_t st, int* count, bool spec_only)
 {
     const int lo = window < 0 ? 0 : window, hi = window < 0 ? p.P : window + 1;
+    if (spec_only) nrhs = 1;
     int n = 0;
     size_t s1, s2, s3;
     int maxb0, maxMM;
     fused_smem(p, lo, hi, &s1, &s2, &s3, &maxb0, &maxMM);
+    ensure_attrs();
     if (maxb0 > 0) {
-        ensure_attrs();
-        dim3 g1(maxb0, hi - lo), g2((maxMM + 31) / 32, hi - lo);
+        dim3 g1(maxb0, hi - lo, nrhs), g2((maxMM + 31) / 32, hi - lo, nrhs);
         k_fwd_yz<<<g1, kT, s1, st>>>(p.wins_dev, lo);
         k_xround<<<g2, kT, s2, st>>>(p.wins_dev, lo, spec_only ? 1 : 0);
         n += 2;
@@ -396,28 +447,33 @@ cudaError_t launch_transforms(const Plan& p, int window, cudaStream_t st, int* c
             ++n;
         }
     }
+    size_t sm[3] = {0, 0, 0};
     for (int s = lo; s < hi; ++s)
-        if (p.win[s].D != 3) n += generic_window(p.win[s], st, spec_only);
+        if (p.win[s].D < 3) sm[p.win[s].D] = std::max(sm[p.win[s].D], small_smem(p.win[s]));
+    if (sm[1] > 0) { k_small_transform<1><<<dim3(hi - lo, nrhs), kT, sm[1], st>>>(p.wins_dev, lo, spec_only ? 1 : 0); ++n; }
+    if (sm[2] > 0) { k_small_transform<2><<<dim3(hi - lo, nrhs), kT, sm[2], st>>>(p.wins_dev, lo, spec_only ? 1 : 0); ++n; }
     if (count) *count = n;
     return cudaGetLastError();
 }
 
 // One window whose descriptor is already in device memory (w_dev) and on the host (w): the same
-// kernels as launch_transforms, without a plan.
+// kernels as launch_transforms, without a plan, one right-hand side.
 cudaError_t launch_transforms_window(const WinDev& w, const WinDev* w_dev, cudaStream_t st)
 {
+    ensure_attrs();
     if (w.D == 3) {
-        ensure_attrs();
         const int b0 = w.box[0], b1 = w.box[1], b2 = w.box[2], M = w.M;
         const size_t s1 = sizeof(float2) * (b2 * M + 2 * b1 * M) + sizeof(float) * b1 * b2;
         const size_t s2 = sizeof(float2) * (b0 * M + b0 * 32) + sizeof(float4) * M * 32;
         const size_t s3 = sizeof(float4) * (M * M + b1 * M) + sizeof(float2) * (b1 + b2) * M;
-        dim3 g1(b0, 1), g2((M * M + 31) / 32, 1);
+        dim3 g1(b0, 1, 1), g2((M * M + 31) / 32, 1, 1);
         k_fwd_yz<<<g1, kT, s1, st>>>(w_dev, 0);
         k_xround<<<g2, kT, s2, st>>>(w_dev, 0, 0);
         k_inv_yz<<<g1, kT, s3, st>>>(w_dev, 0);
+    } else if (w.D == 2) {
+        k_small_transform<2><<<dim3(1, 1), kT, small_smem(w), st>>>(w_dev, 0, 0);
     } else {
-        generic_window(w, st, false);
+        k_small_transform<1><<<dim3(1, 1), kT, small_smem(w), st>>>(w_dev, 0, 0);
     }
     return cudaGetLastError();
 }

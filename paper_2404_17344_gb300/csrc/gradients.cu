@@ -111,14 +111,11 @@ cudaError_t launch_gather_grad(const Plan& p, int pass, const float* other, floa
 {
     int launched = 0;
     for (int s = 0; s < p.P; ++s) {
-        const int D = p.dims[s];
-        const int4* lists[2] = {p.items_fast + p.item_begin_fast[s], p.items_gen + p.item_begin_gen[s]};
-        const int counts[2] = {p.item_begin_fast[s + 1] - p.item_begin_fast[s],
-                               p.item_begin_gen[s + 1] - p.item_begin_gen[s]};
-        for (int q = 0; q < 2; ++q) {
-            if (pass == 0) launched += launch_pass<0>(p, lists[q], counts[q], D, other, ks, grad_x, st);
-            else launched += launch_pass<1>(p, lists[q], counts[q], D, other, ks, grad_x, st);
-        }
+        const std::vector<int>& b = p.item_begin[p.kind[s]];
+        const int4* items = p.items + b[s];
+        const int n = b[s + 1] - b[s];
+        if (pass == 0) launched += launch_pass<0>(p, items, n, p.dims[s], other, ks, grad_x, st);
+        else launched += launch_pass<1>(p, items, n, p.dims[s], other, ks, grad_x, st);
     }
     if (count) *count = launched;
     return cudaGetLastError();

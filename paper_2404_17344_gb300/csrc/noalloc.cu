@@ -178,6 +178,7 @@ extern "C" int addker_fastsum_noalloc(const float* points, int64_t N, int d, dou
         w.lo[t] = 0;
         w.box[t] = t < D ? n : 1;
     }
+    w.gsz = nd;                                                // one right-hand side: slot 0 only
     w.grid = reinterpret_cast<float*>(base + o_grid);
     w.h = reinterpret_cast<float2*>(base + o_h);
     w.buf1 = reinterpret_cast<float4*>(base + o_b1);

@@ -33,7 +33,8 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // Lane (ah, bh, c) accumulates acc[a][p] = (g[4ah+a][4bh+2p][c], g[4ah+a][4bh+2p+1][c]).
 __global__ void __launch_bounds__(kWarps * 32) k_spread3_w8(const int4* __restrict__ items, int nitems,
                                                            const WinDev* __restrict__ wins,
-                                                           const float* __restrict__ v, const WinPoly poly)
+                                                           const float* __restrict__ v, int64_t ldv,
+                                                           const WinPoly poly)
 {
     constexpr int W = 8;
     constexpr int STRIDE = 44;            // 16 + 8 + 16 floats, padded so staging stores avoid conflicts
@@ -45,6 +46,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_spread3_w8(const int4* __restri
     const WinDev& P = wins[it.w];
     const float4* __restrict__ pts = P.pts + it.x;
     const int count = it.y;
+    const int r = blockIdx.y;                                  // right-hand side
+    v += r * ldv;
     const int n = P.n;
     float* ws = sw[warp];
     const int ah = lane >> 4, bh = (lane >> 3) & 1, c = lane & 7;
@@ -110,7 +113,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_spread3_w8(const int4* __restri
     const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff, cz = (it.z >> 16) & 0xff;
     const int ox = cx - 3 - P.lo[0], oy = cy - 3 - P.lo[1], oz = cz - 3 - P.lo[2];
     const int sy = P.box[2], sx = P.box[1] * P.box[2];
-    float* g = P.grid + (size_t)(ox + 4 * ah) * sx + (size_t)(oy + 4 * bh) * sy + oz + c;
+    float* g = P.grid + r * P.gsz + (size_t)(ox + 4 * ah) * sx + (size_t)(oy + 4 * bh) * sy + oz + c;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         float* ga = g + (size_t)a * sx;
@@ -205,7 +208,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_gather3_w8(const int4* __res
                                                               float* __restrict__ outK, float* __restrict__ outD,
                                                               const float* __restrict__ scaleK,
                                                               const float* __restrict__ scaleD, int64_t strideK,
-                                                              int64_t strideD, const WinPoly poly)
+                                                              int64_t strideD, int64_t rstrideK, int64_t rstrideD,
+                                                              const WinPoly poly)
 {
     constexpr int W = 8;
     __shared__ __align__(16) float2 tile[kWarps][W * W * W];
@@ -217,7 +221,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_gather3_w8(const int4* __res
     const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff, cz = (it.z >> 16) & 0xff;
     const int ox = cx - 3 - P.lo[0], oy = cy - 3 - P.lo[1], oz = cz - 3 - P.lo[2];
     const int sy = P.box[2], sx = P.box[1] * P.box[2];
-    const float2* __restrict__ h = P.h + (size_t)ox * sx + (size_t)oy * sy + oz;
+    const int r = blockIdx.y;                                  // right-hand side
+    const float2* __restrict__ h = P.h + r * P.gsz + (size_t)ox * sx + (size_t)oy * sy + oz;
     float2* t = tile[warp];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
@@ -232,13 +237,12 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_gather3_w8(const int4* __res
     const float sD = WD ? scaleD[it.w] : 0.f;
     const int n = P.n;
     // two points per lane while more than 32 remain, then one, so tail lanes do no dead work
+    const int64_t offK = it.w * strideK + r * rstrideK, offD = it.w * strideD + r * rstrideD;
     int base = 0;
     for (; it.y - base > 32; base += 64)
-        gather_points<2, WK, WD>(t4, pts, base + lane, it.y, n, poly, outK, outD, sK, sD,
-                                 (int64_t)it.w * strideK, (int64_t)it.w * strideD);
+        gather_points<2, WK, WD>(t4, pts, base + lane, it.y, n, poly, outK, outD, sK, sD, offK, offD);
     if (base < it.y && base + lane < it.y)
-        gather_points<1, WK, WD>(t4, pts, base + lane, it.y, n, poly, outK, outD, sK, sD,
-                                 (int64_t)it.w * strideK, (int64_t)it.w * strideD);
+        gather_points<1, WK, WD>(t4, pts, base + lane, it.y, n, poly, outK, outD, sK, sD, offK, offD);
 }
 
 // ----------------------------------------------------------------------------------
@@ -283,7 +287,8 @@ __device__ __forceinline__ void warp_transpose_reduce(float* v, int lane, int* b
 template <int D>
 __global__ void __launch_bounds__(kWarps * 32) k_spread_lowd_w8(const int4* __restrict__ items, int nitems,
                                                                const WinDev* __restrict__ wins,
-                                                               const float* __restrict__ v, const WinPoly poly)
+                                                               const float* __restrict__ v, int64_t ldv,
+                                                               const WinPoly poly)
 {
     constexpr int W = 8;
     constexpr int NV = D == 1 ? W : W * W;
@@ -293,6 +298,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_spread_lowd_w8(const int4* __re
     const int4 it = items[item];
     const WinDev& P = wins[it.w];
     const float4* __restrict__ pts = P.pts + it.x;
+    const int r = blockIdx.y;                                  // right-hand side
+    v += r * ldv;
     float acc[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.f;
@@ -332,7 +339,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_spread_lowd_w8(const int4* __re
         for (int e = 0; e < (NV >= 32 ? NV / 32 : 1); ++e) {
             const int idx = base + e;
             const int a = D == 1 ? idx : idx / W, b = D == 1 ? 0 : idx % W;
-            atomicAdd(P.grid + (size_t)(ox + a) * P.box[1] + (D >= 2 ? oy + b : 0), acc[e]);
+            atomicAdd(P.grid + r * P.gsz + (size_t)(ox + a) * P.box[1] + (D >= 2 ? oy + b : 0), acc[e]);
         }
     }
 }
@@ -343,7 +350,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_gather_lowd_w8(const int4* __re
                                                                float* __restrict__ outK, float* __restrict__ outD,
                                                                const float* __restrict__ scaleK,
                                                                const float* __restrict__ scaleD, int64_t strideK,
-                                                               int64_t strideD, const WinPoly poly)
+                                                               int64_t strideD, int64_t rstrideK, int64_t rstrideD,
+                                                               const WinPoly poly)
 {
     constexpr int W = 8;
     constexpr int NV = D == 1 ? W : W * W;
@@ -356,9 +364,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_gather_lowd_w8(const int4* __re
     const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff;
     const int ox = cx - 3 - P.lo[0], oy = cy - 3 - P.lo[1];
     float2* t = tile[warp];
+    const int r = blockIdx.y;                                  // right-hand side
+    const float2* __restrict__ h = P.h + r * P.gsz;
     for (int i = lane; i < NV; i += 32) {
         const int a = D == 1 ? i : i / W, b = D == 1 ? 0 : i % W;
-        t[i] = P.h[(size_t)(ox + a) * P.box[1] + (D >= 2 ? oy + b : 0)];
+        t[i] = h[(size_t)(ox + a) * P.box[1] + (D >= 2 ? oy + b : 0)];
     }
     __syncwarp();
     const float4* __restrict__ pts = P.pts + it.x;
@@ -390,8 +400,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_gather_lowd_w8(const int4* __re
             }
         }
         const int64_t i = (int64_t)__float_as_int(p.w);
-        if (WK) outK[i + (int64_t)it.w * strideK] = sK * f.x;
-        if (WD) outD[i + (int64_t)it.w * strideD] = sD * f.y;
+        if (WK) outK[i + it.w * strideK + r * rstrideK] = sK * f.x;
+        if (WD) outD[i + it.w * strideD + r * rstrideD] = sD * f.y;
     }
 }
 
@@ -401,11 +411,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_gather_lowd_w8(const int4* __re
 template <int D>
 __global__ void __launch_bounds__(128) k_spread_generic(const int4* __restrict__ items,
                                                         const WinDev* __restrict__ wins,
-                                                        const float* __restrict__ v, const WinPoly poly)
+                                                        const float* __restrict__ v, int64_t ldv,
+                                                        const WinPoly poly)
 {
     __shared__ float box[kMaxW * kMaxW * kMaxW];
     const int4 it = items[blockIdx.x];
     const WinDev& P = wins[it.w];
+    const int r = blockIdx.y;                                  // right-hand side
+    v += r * ldv;
     const int W = 2 * P.m;
     int WD = W;
     if (D >= 2) WD *= W;
@@ -438,7 +451,7 @@ __global__ void __launch_bounds__(128) k_spread_generic(const int4* __restrict__
         if (D == 2) { a = i / W; bb = i % W; }
         if (D == 3) { a = i / (W * W); bb = (i / W) % W; cc = i % W; }
         const size_t g = ((size_t)(ox + a) * P.box[1] + (D >= 2 ? oy + bb : 0)) * P.box[2] + (D >= 3 ? oz + cc : 0);
-        if (box[i] != 0.f) atomicAdd(P.grid + g, box[i]);
+        if (box[i] != 0.f) atomicAdd(P.grid + r * P.gsz + g, box[i]);
     }
 }
 
@@ -448,11 +461,14 @@ __global__ void __launch_bounds__(128) k_gather_generic(const int4* __restrict__
                                                         float* __restrict__ outK, float* __restrict__ outD,
                                                         const float* __restrict__ scaleK,
                                                         const float* __restrict__ scaleD, int64_t strideK,
-                                                        int64_t strideD, const WinPoly poly)
+                                                        int64_t strideD, int64_t rstrideK, int64_t rstrideD,
+                                                        const WinPoly poly)
 {
     const int4 it = items[blockIdx.x];
     const WinDev& P = wins[it.w];
     const int W = 2 * P.m;
+    const int r = blockIdx.y;                                  // right-hand side
+    const float2* __restrict__ h = P.h + r * P.gsz;
     const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff, cz = (it.z >> 16) & 0xff;
     const int ox = cx - P.m + 1 - P.lo[0], oy = cy - P.m + 1 - P.lo[1], oz = cz - P.m + 1 - P.lo[2];
     for (int k = threadIdx.x; k < it.y; k += blockDim.x) {
@@ -470,7 +486,7 @@ __global__ void __launch_bounds__(128) k_gather_generic(const int4* __restrict__
                 for (int cc = 0; cc < (D >= 3 ? W : 1); ++cc) {
                     const size_t g = ((size_t)(ox + a) * P.box[1] + (D >= 2 ? oy + bb : 0)) * P.box[2] +
                                      (D >= 3 ? oz + cc : 0);
-                    const float2 hv = P.h[g];
+                    const float2 hv = h[g];
                     const float wc = D >= 3 ? w2[cc] : 1.f;
                     tK = fmaf(hv.x, wc, tK);
                     tD = fmaf(hv.y, wc, tD);
@@ -483,44 +499,41 @@ __global__ void __launch_bounds__(128) k_gather_generic(const int4* __restrict__
             fD = fmaf(uD, w0[a], fD);
         }
         const int64_t i = (int64_t)__float_as_int(p.w);
-        if (WK) outK[i + (int64_t)it.w * strideK] = scaleK[it.w] * fK;
-        if (WD) outD[i + (int64_t)it.w * strideD] = scaleD[it.w] * fD;
+        if (WK) outK[i + it.w * strideK + r * rstrideK] = scaleK[it.w] * fK;
+        if (WD) outD[i + it.w * strideD + r * rstrideD] = scaleD[it.w] * fD;
     }
 }
 
 }  // namespace
 
-// Item ranges: items of window s are [begin[s], begin[s+1]) in each list; window < 0 = all.
-static void item_range(const std::vector<int>& begin, int window, int* lo, int* hi)
+// Items of one kind for one window, or for all windows (window < 0).
+static void item_range(const Plan& p, int kind, int window, int* lo, int* hi)
 {
-    if (window < 0) { *lo = begin.front(); *hi = begin.back(); }
-    else { *lo = begin[window]; *hi = begin[window + 1]; }
+    const std::vector<int>& b = p.item_begin[kind];
+    if (window < 0) { *lo = b.front(); *hi = b.back(); }
+    else { *lo = b[window]; *hi = b[window + 1]; }
 }
 
-cudaError_t launch_spread(const Plan& p, int window, const float* v, cudaStream_t st, int* count)
+// One launch per kernel kind that has items: all windows of a kind together, all right-hand sides
+// along gridDim.y.
+cudaError_t launch_spread(const Plan& p, int window, const float* v, int64_t ldv, int nrhs, cudaStream_t st, int* count)
 {
     int launched = 0;
     const WinDev* wd = p.wins_dev;
-    int lo, hi;
-    item_range(p.item_begin_fast, window, &lo, &hi);
-    if (hi > lo) {
+    for (int k = 0; k < kKinds; ++k) {
+        int lo, hi;
+        item_range(p, k, window, &lo, &hi);
+        if (hi <= lo) continue;
         const int n = hi - lo;
-        k_spread3_w8<<<(n + kWarps - 1) / kWarps, kWarps * 32, 0, st>>>(p.items_fast + lo, n, wd, v, p.poly);
-        ++launched;
-    }
-    const std::vector<int>& gb = p.item_begin_gen;
-    for (int s = 0; s < p.P; ++s) {
-        if (window >= 0 && s != window) continue;
-        const int n = gb[s + 1] - gb[s];
-        if (n == 0) continue;
-        const int4* it = p.items_gen + gb[s];
-        const int nb = (n + kWarps - 1) / kWarps;
-        if (p.m == 4 && p.dims[s] == 1) k_spread_lowd_w8<1><<<nb, kWarps * 32, 0, st>>>(it, n, wd, v, p.poly);
-        else if (p.m == 4 && p.dims[s] == 2) k_spread_lowd_w8<2><<<nb, kWarps * 32, 0, st>>>(it, n, wd, v, p.poly);
-        else switch (p.dims[s]) {
-            case 1: k_spread_generic<1><<<n, 128, 0, st>>>(it, wd, v, p.poly); break;
-            case 2: k_spread_generic<2><<<n, 128, 0, st>>>(it, wd, v, p.poly); break;
-            default: k_spread_generic<3><<<n, 128, 0, st>>>(it, wd, v, p.poly); break;
+        const int4* it = p.items + lo;
+        const dim3 warps((n + kWarps - 1) / kWarps, nrhs), blocks(n, nrhs);
+        switch (k) {
+            case kKindFast3: k_spread3_w8<<<warps, kWarps * 32, 0, st>>>(it, n, wd, v, ldv, p.poly); break;
+            case kKindLow1: k_spread_lowd_w8<1><<<warps, kWarps * 32, 0, st>>>(it, n, wd, v, ldv, p.poly); break;
+            case kKindLow2: k_spread_lowd_w8<2><<<warps, kWarps * 32, 0, st>>>(it, n, wd, v, ldv, p.poly); break;
+            case kKindGen1: k_spread_generic<1><<<blocks, 128, 0, st>>>(it, wd, v, ldv, p.poly); break;
+            case kKindGen2: k_spread_generic<2><<<blocks, 128, 0, st>>>(it, wd, v, ldv, p.poly); break;
+            default: k_spread_generic<3><<<blocks, 128, 0, st>>>(it, wd, v, ldv, p.poly); break;
         }
         ++launched;
     }
@@ -529,47 +542,52 @@ cudaError_t launch_spread(const Plan& p, int window, const float* v, cudaStream_
 }
 
 template <bool WK, bool WD>
-static int gather_all(const Plan& p, int window, float* outK, int64_t zK, float* outD, int64_t zD,
-                      const float* sK, const float* sD, cudaStream_t st)
+static int gather_all(const Plan& p, int window, float* oK, int64_t zK, int64_t rK, float* oD, int64_t zD,
+                      int64_t rD, int nrhs, const float* sK, const float* sD, cudaStream_t st)
 {
     int launched = 0;
     const WinDev* wd = p.wins_dev;
-    int lo, hi;
-    item_range(p.item_begin_fast, window, &lo, &hi);
-    if (hi > lo) {
+    for (int k = 0; k < kKinds; ++k) {
+        int lo, hi;
+        item_range(p, k, window, &lo, &hi);
+        if (hi <= lo) continue;
         const int n = hi - lo;
-        k_gather3_w8<WK, WD><<<(n + kWarps - 1) / kWarps, kWarps * 32, 0, st>>>(p.items_fast + lo, n, wd, outK, outD,
-                                                                               sK, sD, zK, zD, p.poly);
-        ++launched;
-    }
-    const std::vector<int>& gb = p.item_begin_gen;
-    for (int s = 0; s < p.P; ++s) {
-        if (window >= 0 && s != window) continue;
-        const int n = gb[s + 1] - gb[s];
-        if (n == 0) continue;
-        const int4* it = p.items_gen + gb[s];
-        const int nb = (n + kWarps - 1) / kWarps;
-        if (p.m == 4 && p.dims[s] == 1)
-            k_gather_lowd_w8<1, WK, WD><<<nb, kWarps * 32, 0, st>>>(it, n, wd, outK, outD, sK, sD, zK, zD, p.poly);
-        else if (p.m == 4 && p.dims[s] == 2)
-            k_gather_lowd_w8<2, WK, WD><<<nb, kWarps * 32, 0, st>>>(it, n, wd, outK, outD, sK, sD, zK, zD, p.poly);
-        else switch (p.dims[s]) {
-            case 1: k_gather_generic<1, WK, WD><<<n, 128, 0, st>>>(it, wd, outK, outD, sK, sD, zK, zD, p.poly); break;
-            case 2: k_gather_generic<2, WK, WD><<<n, 128, 0, st>>>(it, wd, outK, outD, sK, sD, zK, zD, p.poly); break;
-            default: k_gather_generic<3, WK, WD><<<n, 128, 0, st>>>(it, wd, outK, outD, sK, sD, zK, zD, p.poly); break;
+        const int4* it = p.items + lo;
+        const dim3 warps((n + kWarps - 1) / kWarps, nrhs), blocks(n, nrhs);
+        switch (k) {
+            case kKindFast3:
+                k_gather3_w8<WK, WD><<<warps, kWarps * 32, 0, st>>>(it, n, wd, oK, oD, sK, sD, zK, zD, rK, rD, p.poly);
+                break;
+            case kKindLow1:
+                k_gather_lowd_w8<1, WK, WD><<<warps, kWarps * 32, 0, st>>>(it, n, wd, oK, oD, sK, sD, zK, zD, rK, rD,
+                                                                          p.poly);
+                break;
+            case kKindLow2:
+                k_gather_lowd_w8<2, WK, WD><<<warps, kWarps * 32, 0, st>>>(it, n, wd, oK, oD, sK, sD, zK, zD, rK, rD,
+                                                                          p.poly);
+                break;
+            case kKindGen1:
+                k_gather_generic<1, WK, WD><<<blocks, 128, 0, st>>>(it, wd, oK, oD, sK, sD, zK, zD, rK, rD, p.poly);
+                break;
+            case kKindGen2:
+                k_gather_generic<2, WK, WD><<<blocks, 128, 0, st>>>(it, wd, oK, oD, sK, sD, zK, zD, rK, rD, p.poly);
+                break;
+            default:
+                k_gather_generic<3, WK, WD><<<blocks, 128, 0, st>>>(it, wd, oK, oD, sK, sD, zK, zD, rK, rD, p.poly);
+                break;
         }
         ++launched;
     }
     return launched;
 }
 
-cudaError_t launch_gather(const Plan& p, int window, float* outK, int64_t zK, float* outD, int64_t zD,
-                          const float* sK, const float* sD, cudaStream_t st, int* count)
+cudaError_t launch_gather(const Plan& p, int window, float* outK, int64_t zK, int64_t rK, float* outD, int64_t zD,
+                          int64_t rD, int nrhs, const float* sK, const float* sD, cudaStream_t st, int* count)
 {
     int launched = 0;
-    if (outK && outD) launched = gather_all<true, true>(p, window, outK, zK, outD, zD, sK, sD, st);
-    else if (outK) launched = gather_all<true, false>(p, window, outK, zK, nullptr, 0, sK, sD, st);
-    else if (outD) launched = gather_all<false, true>(p, window, nullptr, 0, outD, zD, sK, sD, st);
+    if (outK && outD) launched = gather_all<true, true>(p, window, outK, zK, rK, outD, zD, rD, nrhs, sK, sD, st);
+    else if (outK) launched = gather_all<true, false>(p, window, outK, zK, rK, nullptr, 0, 0, nrhs, sK, sD, st);
+    else if (outD) launched = gather_all<false, true>(p, window, nullptr, 0, 0, outD, zD, rD, nrhs, sK, sD, st);
     if (count) *count = launched;
     return cudaGetLastError();
 }

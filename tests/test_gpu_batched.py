@@ -1,0 +1,142 @@
+"""Several right-hand sides per launch: every stage of the product processes up to eight right-hand
+sides in one launch per kernel kind (each with its own grid slot), larger batches in chunks. Results
+must match the single-right-hand-side path column by column and the FP64 oracle, for every kernel kind
+(3-D fast, 1-D/2-D fast, generic) and every product selector, across chunk boundaries and slot growth.
+
+Tolerance: relative L2 1e-5 as for the single products (grid sums use atomics, so repeated products
+agree to FP32 rounding, not bitwise)."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import fastsum
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch
+
+
+def make_op(torch, wl, **kw):
+    from paper_2404_17344_gb300 import AddKer
+    return AddKer(torch.from_numpy(wl.points).cuda(), wl.windows, wl.ell, wl.sigma_f, wl.bandwidth, wl.cutoff, **kw)
+
+
+def columns_one_by_one(op, V):
+    Ks, Ds = [], []
+    for j in range(V.shape[1]):
+        k, d = op.matvec_all(V[:, j].contiguous())
+        Ks.append(k.cpu().numpy())
+        Ds.append(d.cpu().numpy())
+    return np.stack(Ks, 1), np.stack(Ds, 2)
+
+
+@pytest.mark.parametrize("cfg,N,nrhs", [("c3", 3000, 11), ("c1", 6000, 8), ("c2", 4000, 3)])
+def test_batched_matches_single_and_oracle(torch_cuda, cfg, N, nrhs):
+    torch = torch_cuda
+    wl = workloads.make(cfg, N=N)
+    wl.sigma_f = 1.3
+    V = torch.from_numpy(wl.vector(nrhs=nrhs)).cuda()
+    op = make_op(torch, wl)
+    Kv, dK = op.matvec_all(V)
+    K1, D1 = columns_one_by_one(op, V)
+    assert rel(Kv.cpu(), K1) < TOL
+    assert rel(dK.cpu(), D1) < TOL
+    for j in (0, nrhs - 1):                      # first chunk and last (possibly partial) chunk
+        Kr, dKr = fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f,
+                                     V[:, j].cpu().numpy().astype(np.float64), wl.bandwidth, wl.cutoff)
+        assert rel(Kv[:, j].cpu(), Kr) < TOL
+        for s in range(wl.P):
+            assert rel(dK[s, :, j].cpu(), dKr[s]) < TOL, (j, s)
+
+
+def test_batched_selectors_mixed_windows(torch_cuda):
+    from paper_2404_17344_gb300 import ADDKER_ELL, ADDKER_ELL_SHARED, ADDKER_SIGMA_F
+    torch = torch_cuda
+    wl = workloads.make("c3", N=2500)
+    wl.sigma_f = 0.8
+    nrhs = 10
+    V = torch.from_numpy(wl.vector(nrhs=nrhs)).cuda()
+    op = make_op(torch, wl)
+    Kv, dK = op.matvec_all(V)
+    assert rel(op.matvec(V).cpu(), Kv.cpu()) < TOL
+    for s in range(wl.P):
+        assert rel(op.dmatvec(ADDKER_ELL(s), V).cpu(), dK[s].cpu()) < TOL, s
+    assert rel(op.dmatvec(ADDKER_ELL_SHARED, V).cpu(), dK.sum(0).cpu()) < TOL
+    assert rel(op.dmatvec(ADDKER_SIGMA_F, V).cpu(), (2.0 / wl.sigma_f) * Kv.cpu()) < TOL
+
+
+def test_slot_growth_keeps_results(torch_cuda):
+    """Slots grow 1 -> 4 -> 8 as batches grow; products before and after agree."""
+    torch = torch_cuda
+    wl = workloads.make("c3", N=2000)
+    V = torch.from_numpy(wl.vector(nrhs=9)).cuda()
+    op = make_op(torch, wl)
+    k_first, d_first = op.matvec_all(V[:, 0].contiguous())
+    K3, D3 = op.matvec_all(V[:, :3].contiguous())
+    K9, D9 = op.matvec_all(V)
+    k_last, d_last = op.matvec_all(V[:, 0].contiguous())
+    assert rel(K3[:, 0].cpu(), k_first.cpu()) < TOL and rel(D3[:, :, 0].cpu(), d_first.cpu()) < TOL
+    assert rel(K9[:, :3].cpu(), K3.cpu()) < TOL and rel(D9[:, :, :3].cpu(), D3.cpu()) < TOL
+    assert rel(k_last.cpu(), k_first.cpu()) < TOL and rel(d_last.cpu(), d_first.cpu()) < TOL
+
+
+def test_batched_generic_cutoff(torch_cuda):
+    """m = 3: the generic kernels of every dimension, batched."""
+    torch = torch_cuda
+    wl = workloads.make("c3", N=1500)
+    wl.cutoff = 3
+    V = torch.from_numpy(wl.vector(nrhs=5)).cuda()
+    op = make_op(torch, wl)
+    Kv, dK = op.matvec_all(V)
+    K1, D1 = columns_one_by_one(op, V)
+    assert rel(Kv.cpu(), K1) < TOL and rel(dK.cpu(), D1) < TOL
+    Kr, dKr = fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f, V[:, 4].cpu().numpy().astype(np.float64),
+                                 wl.bandwidth, wl.cutoff)
+    assert rel(Kv[:, 4].cpu(), Kr) < TOL and rel(dK[:, :, 4].cpu(), dKr) < TOL
+
+
+def test_largest_small_transform(torch_cuda):
+    """1-D and 2-D windows at the largest bandwidth (M = 64): the single-block transform with its
+    largest shared-memory footprint."""
+    torch = torch_cuda
+    wl = workloads.tiny(N=3000, d=3, windows=[(0, 1), (2,)], ell=[0.3, 0.2])
+    wl.bandwidth = [64, 64]
+    wl.cutoff = 4
+    V = torch.from_numpy(wl.vector(nrhs=2)).cuda()
+    op = make_op(torch, wl)
+    Kv, dK = op.matvec_all(V)
+    for j in range(2):
+        Kr, dKr = fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f,
+                                     V[:, j].cpu().numpy().astype(np.float64), wl.bandwidth, wl.cutoff)
+        assert rel(Kv[:, j].cpu(), Kr) < TOL and rel(dK[:, :, j].cpu(), dKr) < TOL
+
+
+def test_host_entry_batched(torch_cuda):
+    torch = torch_cuda
+    wl = workloads.make("c3", N=2000)
+    nrhs = 9
+    v = wl.vector(nrhs=nrhs)                     # (N, nrhs)
+    op = make_op(torch, wl)
+    Kd, dKd = op.matvec_all(torch.from_numpy(v).cuda())
+    vh = torch.from_numpy(np.ascontiguousarray(v.T)).reshape(-1).pin_memory()
+    Kh = torch.empty(wl.N * nrhs).pin_memory()
+    dKh = torch.empty(wl.N * wl.P * nrhs).pin_memory()
+    op.matvec_all_host(vh, Kh, dKh, nrhs)
+    assert rel(Kh.reshape(nrhs, wl.N).t(), Kd.cpu()) < TOL
+    assert rel(dKh.reshape(nrhs, wl.P, wl.N).permute(1, 2, 0), dKd.cpu()) < TOL
