@@ -234,6 +234,7 @@ __global__ void k_twiddles(float2* __restrict__ tf, float2* __restrict__ ti, int
 __global__ void k_window_sum(const float* __restrict__ ks, int P, int64_t N, float scale, float* __restrict__ out,
                              int64_t ld, int vec)
 {
+    grid_dep_wait();
     const int64_t i0 = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
     if (i0 >= N) return;
     ks += blockIdx.y * (int64_t)P * N;                         // right-hand side blockIdx.y
@@ -261,6 +262,7 @@ struct ThetaScale {
 // grad_theta[s] = sigma_f^2 (2/ell_s) dots[P + s]  (s < P);  grad_theta[P] = 2 sigma_f sum_s dots[s]
 __global__ void k_theta_grad(const double* __restrict__ dots, int P, ThetaScale sc, double* __restrict__ out)
 {
+    grid_dep_wait();
     const int s = threadIdx.x;
     if (s < P) out[s] = sc.s[s] * dots[P + s];
     if (s == 0) {
@@ -292,6 +294,7 @@ __global__ void k_max_norm(const float* __restrict__ X, int64_t N, int d, const 
 
 __global__ void k_scale(const float* __restrict__ X, int64_t n, float f, float* __restrict__ Y)
 {
+    grid_dep_wait();
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) Y[i] = X[i] * f;
 }
@@ -746,7 +749,8 @@ int ensure_slots(Plan& p, int want)
 void window_sum(Plan& p, int R, float scale, float* out, int64_t ld, cudaStream_t st)
 {
     const dim3 grid(grid_blocks((p.N + 3) / 4, 256), R);
-    k_window_sum<<<grid, 256, 0, st>>>(p.ks, p.P, p.N, scale, out, ld, vec_ok(p, out, ld));
+    launch_k(true, k_window_sum, grid, dim3(256), 0, st, (const float*)p.ks, p.P, p.N, scale, out, ld,
+             vec_ok(p, out, ld));
 }
 
 // One product for R <= slots right-hand sides v + r ldv (r < R), every stage one launch per kernel kind.
@@ -1073,7 +1077,8 @@ int addker_dmatvec(addker_plan* plan, int param, const float* v, float* out, int
     if (param == ADDKER_ELL_SHARED) return product_all(p, v, nrhs, out, nullptr, -1, 2);
     CS(product_all(p, v, nrhs, out, nullptr, -1, 0));
     const int64_t len = p.N * (int64_t)nrhs;
-    k_scale<<<grid_blocks(len, 256), 256, 0, p.stream>>>(out, len, (float)(2.0 / p.sigma_f), out);
+    launch_k(true, k_scale, dim3(grid_blocks(len, 256)), dim3(256), 0, p.stream, (const float*)out, len,
+             (float)(2.0 / p.sigma_f), out);
     CK(cudaGetLastError());
     return ADDKER_OK;
 }
@@ -1099,14 +1104,15 @@ int addker_vjp(addker_plan* plan, const float* v, const float* w, float* grad_v,
             if (p.P > 1)
                 window_sum(p, 1, (float)(p.sigma_f * p.sigma_f), grad_v, p.N, st);
             else
-                k_scale<<<grid_blocks(p.N, 256), 256, 0, st>>>(grad_v, p.N, (float)(p.sigma_f * p.sigma_f), grad_v);
+                launch_k(true, k_scale, dim3(grid_blocks(p.N, 256)), dim3(256), 0, st, (const float*)grad_v,
+                         p.N, (float)(p.sigma_f * p.sigma_f), grad_v);
             CK(cudaGetLastError());
         }
     }
     ThetaScale sc;
     for (int s = 0; s < p.P; ++s) sc.s[s] = p.sigma_f * p.sigma_f * 2.0 / p.ell[s];
     sc.s[p.P] = 2.0 * p.sigma_f;
-    k_theta_grad<<<1, 64, 0, st>>>(p.dots, p.P, sc, grad_theta);
+    launch_k(true, k_theta_grad, dim3(1), dim3(64), 0, st, (const double*)p.dots, p.P, sc, grad_theta);
     CK(cudaGetLastError());
     return ADDKER_OK;
 }
@@ -1269,7 +1275,8 @@ int addker_debug_stage(addker_plan* plan, int window, int stage, const float* v,
         }
         return ADDKER_OK;
     }
-    CK(launch_transforms(p, window, 1, st, nullptr, true));           // consumes (re-zeroes) the grid
+    CK(launch_transforms(p, window, 1, st, nullptr, true));
+    CK(cudaMemsetAsync(w.grid, 0, sizeof(float) * gsz, st));        // d = 3: the inverse pass that clears it did not run
     std::vector<float4> s(md);
     CK(cudaMemcpyAsync(s.data(), w.spec, sizeof(float4) * md, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

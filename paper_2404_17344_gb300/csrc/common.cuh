@@ -105,6 +105,58 @@ struct Plan {
     double* dots = nullptr;               // 2P doubles: gradient dot products (addker_vjp)
 };
 
+// Launch a kernel on st. With pdl the launch carries the programmatic-serialisation attribute (the
+// kernel orders its own accesses with grid_dep_wait()); only for kernels whose predecessor in the
+// stream is a kernel of the same product.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args... args)
+{
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = pdl ? &attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// ---- asynchronous staging and launch overlap (inline PTX, sm_90 and later) --------------------
+// cp.async: global -> shared copies that do not hold a register; cp_async_wait_all() then a barrier
+// makes them visible to the block. Sizes 4, 8 (both .ca) and 16 bytes (.cg), naturally aligned.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Programmatic dependent launch. The transform kernels, the window sum and the scalings are launched
+// with the programmatic-serialisation attribute, so each launch overlaps the end of its predecessor
+// (which triggers implicitly on completion: triggering at block start measured slower, because the
+// waiting blocks then occupy the SMs). grid_dep_wait() blocks until every prerequisite grid has
+// completed and its writes are visible; such a kernel calls it before it reads or writes anything an
+// earlier kernel touches. The spread and gather kernels (thousands of blocks) are launched plainly:
+// the wait in every warp cost them more than the overlap saved.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 // ---- device window weights ------------------------------------------------------------
 // The W = 2m weights of one coordinate x on a grid of n points; *cell = floor(n x) + n/2.
 __device__ __forceinline__ void window_pair(const WinPoly& P, int q, float u, float u2, float* lo, float* hi)

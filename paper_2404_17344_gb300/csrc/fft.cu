@@ -13,7 +13,7 @@
 //   k_xround   per column:   t[x][c] -> S[kx][c] -> B[x][c]      (x forward, multiply, x inverse)
 //   k_inv_yz   per x-slab:   B[x][ky][kz] -> h[x][y][z]          (y then z inverse, real part)
 // The x round trip fuses forward DFT, multiplication and inverse DFT because all three act on the
-// same column (ky, kz). D = 1, 2 use k_small_transform: one block per window does every pass.
+// same column (ky, kz); k_inv_yz also clears the consumed spread grid. D = 1, 2 use k_small_transform: one block per window does every pass.
 // Each right-hand side has its own slot in every buffer (blockIdx.z, or blockIdx.y for the small
 // kernel), so one launch transforms up to kMaxRhsChunk right-hand sides of all windows.
 #include "common.cuh"
@@ -35,62 +35,90 @@ __device__ __forceinline__ float2 cmadc(float2 a, float2 w, float2 c)     // c +
 // Each phase is a small dense complex matrix product done from shared memory, one 2x2 block of
 // outputs per thread, so each pair of 16-byte shared loads feeds 16 to 32 FMAs. Twiddles are the
 // forward tables twf[axis][l][k] = e^{-2 pi i k l/n}; the inverse uses their conjugates.
-constexpr int kT = 256;
+// The work is tiny (about 1e8 FMAs per product) and latency-bound, so it is spread over many small
+// blocks: each x-slab is split over kSplit blocks (k_fwd_yz by kz columns, k_inv_yz by y rows, with
+// no repeated arithmetic), and k_xround takes kTile columns per block.
+constexpr int kT = 256;                   // threads of the single-block d < 3 transform
+constexpr int kT3 = 128;                  // threads of the d = 3 blocks
+constexpr int kSplit = 4;                 // blocks per x-slab
+constexpr int kTile = 16;                 // columns (ky, kz) per k_xround block
 
-// block = (x, window). smem: gs[b1][b2] float, tz[b2][M], ty[b1][M], t1[b1][M] float2.
-//   t1[y][kz] = sum_z g[x][y][z] tz[z][kz];   out[x][ky][kz] = sum_y ty[y][ky] t1[y][kz]
-// The grid slab is zeroed once read, so d = 3 grids need no separate clearing before a spread.
-__global__ void __launch_bounds__(kT) k_fwd_yz(const WinDev* __restrict__ wins, int w0)
+// Pair range [lo, hi) of part `part` when `pairs` pairs are dealt out to kSplit parts.
+__host__ __device__ inline void part_range(int pairs, int part, int* lo, int* hi)
+{
+    const int per = (pairs + kSplit - 1) / kSplit;
+    *lo = min(pairs, part * per);
+    *hi = min(pairs, *lo + per);
+}
+
+// Shared memory of the three kernels for one box (b0, b1, b2) and bandwidth M.
+__host__ __device__ inline void fused3_smem(int b0, int b1, int b2, int M, size_t* s)
+{
+    const int kw = 2 * ((M / 2 + kSplit - 1) / kSplit);                 // kz columns per k_fwd_yz block
+    const int ny = 2 * (((b1 + 1) / 2 + kSplit - 1) / kSplit);           // y rows per k_inv_yz block
+    s[0] = sizeof(float2) * (b2 * kw + b1 * M + b1 * kw) + sizeof(float) * b1 * b2;
+    s[1] = sizeof(float2) * (b0 * M + b0 * kTile) + sizeof(float4) * M * kTile;
+    s[2] = sizeof(float4) * (M * M + ny * M) + sizeof(float2) * (ny + b2) * M;
+}
+
+// block = (x-slab and kz part, window, rhs). smem: tz[b2][kw], ty[b1][M], t1[b1][kw] float2, gs[b1][b2].
+//   t1[y][k] = sum_z g[x][y][z] tz[z][k];   out[x][ky][k] = sum_y ty[y][ky] t1[y][k]
+// for the block's kz columns k.
+__global__ void __launch_bounds__(kT3) k_fwd_yz(const WinDev* __restrict__ wins, int w0)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const WinDev& W = wins[w0 + blockIdx.y];
     if (W.D != 3) return;
-    const int x = blockIdx.x;
+    const int x = blockIdx.x / kSplit, part = blockIdx.x % kSplit;
     const int b0 = W.box[0], b1 = W.box[1], b2 = W.box[2], M = W.M;
     if (x >= b0) return;
-    float2* tz = reinterpret_cast<float2*>(smem);
-    float2* ty = tz + b2 * M;
-    float2* t1 = ty + b1 * M;
-    float* gs = reinterpret_cast<float*>(t1 + b1 * M);
-    const int r = blockIdx.z;                                  // right-hand-side slot
-    float* g = W.grid + r * W.gsz + (size_t)x * b1 * b2;
-    for (int i = threadIdx.x; i < b1 * b2; i += kT) {
-        gs[i] = g[i];
-        g[i] = 0.f;                      // the slab is consumed: leave the grid zeroed for the next spread
-    }
-    for (int i = threadIdx.x; i < b2 * M; i += kT) tz[i] = W.twf[2][i];
-    for (int i = threadIdx.x; i < b1 * M; i += kT) ty[i] = W.twf[1][i];
-    __syncthreads();
     const int Mh = M / 2;
-    // phase 1: rows y (2 per block, clamped), columns kz (2 per block)
+    int p0, p1;
+    part_range(Mh, part, &p0, &p1);
+    const int np = p1 - p0;
+    if (np <= 0) return;
+    const int kw = 2 * np, kb = 2 * p0;                         // columns kz in [kb, kb + kw)
+    float2* tz = reinterpret_cast<float2*>(smem);
+    float2* ty = tz + b2 * kw;
+    float2* t1 = ty + b1 * M;
+    float* gs = reinterpret_cast<float*>(t1 + b1 * kw);
+    const int r = blockIdx.z;                                  // right-hand-side slot
+    for (int i = threadIdx.x; i < b2 * kw; i += kT3) cp_async8(tz + i, W.twf[2] + (i / kw) * M + kb + i % kw);
+    for (int i = threadIdx.x; i < b1 * M; i += kT3) cp_async8(ty + i, W.twf[1] + i);
+    grid_dep_wait();                                           // the spread grid is complete from here on
+    const float* g = W.grid + r * W.gsz + (size_t)x * b1 * b2;
+    for (int i = threadIdx.x; i < b1 * b2; i += kT3) cp_async4(gs + i, g + i);
+    cp_async_wait_all();
+    __syncthreads();
+    // phase 1: rows y (2 per thread, clamped), columns k (2 per thread)
     const int nb1 = (b1 + 1) / 2;
-    for (int o = threadIdx.x; o < nb1 * Mh; o += kT) {
-        const int y0 = 2 * (o / Mh), y1 = min(y0 + 1, b1 - 1), k0 = 2 * (o % Mh);
+    for (int o = threadIdx.x; o < nb1 * np; o += kT3) {
+        const int y0 = 2 * (o / np), y1 = min(y0 + 1, b1 - 1), k0 = 2 * (o % np);
         float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
         const float* r0 = gs + y0 * b2;
         const float* r1 = gs + y1 * b2;
 #pragma unroll 4
         for (int z = 0; z < b2; ++z) {
-            const float4 w = *reinterpret_cast<const float4*>(tz + z * M + k0);
+            const float4 w = *reinterpret_cast<const float4*>(tz + z * kw + k0);
             const float g0 = r0[z], g1 = r1[z];
             a00.x = fmaf(g0, w.x, a00.x); a00.y = fmaf(g0, w.y, a00.y);
             a01.x = fmaf(g0, w.z, a01.x); a01.y = fmaf(g0, w.w, a01.y);
             a10.x = fmaf(g1, w.x, a10.x); a10.y = fmaf(g1, w.y, a10.y);
             a11.x = fmaf(g1, w.z, a11.x); a11.y = fmaf(g1, w.w, a11.y);
         }
-        *reinterpret_cast<float4*>(t1 + y0 * M + k0) = make_float4(a00.x, a00.y, a01.x, a01.y);
-        if (y0 + 1 < b1) *reinterpret_cast<float4*>(t1 + y1 * M + k0) = make_float4(a10.x, a10.y, a11.x, a11.y);
+        *reinterpret_cast<float4*>(t1 + y0 * kw + k0) = make_float4(a00.x, a00.y, a01.x, a01.y);
+        if (y0 + 1 < b1) *reinterpret_cast<float4*>(t1 + y1 * kw + k0) = make_float4(a10.x, a10.y, a11.x, a11.y);
     }
     __syncthreads();
-    // phase 2: rows ky, columns kz (2x2 blocks)
-    float2* out = reinterpret_cast<float2*>(W.buf1 + r * W.b1sz) + (size_t)x * M * M;
-    for (int o = threadIdx.x; o < Mh * Mh; o += kT) {
-        const int ky = 2 * (o / Mh), kz = 2 * (o % Mh);
+    // phase 2: rows ky, columns k (2x2 blocks)
+    float2* out = reinterpret_cast<float2*>(W.buf1 + r * W.b1sz) + (size_t)x * M * M + kb;
+    for (int o = threadIdx.x; o < Mh * np; o += kT3) {
+        const int ky = 2 * (o / np), k = 2 * (o % np);
         float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
 #pragma unroll 4
         for (int y = 0; y < b1; ++y) {
             const float4 w = *reinterpret_cast<const float4*>(ty + y * M + ky);   // ty[y][ky], ty[y][ky+1]
-            const float4 t = *reinterpret_cast<const float4*>(t1 + y * M + kz);   // t1[y][kz], t1[y][kz+1]
+            const float4 t = *reinterpret_cast<const float4*>(t1 + y * kw + k);   // t1[y][k], t1[y][k+1]
             const float2 w0 = make_float2(w.x, w.y), w1 = make_float2(w.z, w.w);
             const float2 s0 = make_float2(t.x, t.y), s1 = make_float2(t.z, t.w);
             a00 = cmad(s0, w0, a00);
@@ -98,44 +126,50 @@ __global__ void __launch_bounds__(kT) k_fwd_yz(const WinDev* __restrict__ wins, 
             a10 = cmad(s0, w1, a10);
             a11 = cmad(s1, w1, a11);
         }
-        *reinterpret_cast<float4*>(out + ky * M + kz) = make_float4(a00.x, a00.y, a01.x, a01.y);
-        *reinterpret_cast<float4*>(out + (ky + 1) * M + kz) = make_float4(a10.x, a10.y, a11.x, a11.y);
+        *reinterpret_cast<float4*>(out + ky * M + k) = make_float4(a00.x, a00.y, a01.x, a01.y);
+        *reinterpret_cast<float4*>(out + (ky + 1) * M + k) = make_float4(a10.x, a10.y, a11.x, a11.y);
     }
 }
 
-// block = (column tile of 32 columns c = (ky, kz), window). smem: tx[b0][M] float2, ts[b0][32]
-// float2, ss[M][32] float4.
+// block = (tile of kTile columns c = (ky, kz), window, rhs). smem: tx[b0][M] float2, ts[b0][kTile]
+// float2, ss[M][kTile] float4.
 //   S[kx][c] = m_k sum_x tx[x][kx] t[x][c];   B[x][c] = sum_kx conj(tx[x][kx]) S[kx][c]
 // spec_only: write S (multiplied by dconv) to W.spec and stop.
-__global__ void __launch_bounds__(kT) k_xround(const WinDev* __restrict__ wins, int w0, int spec_only)
+__global__ void __launch_bounds__(kT3) k_xround(const WinDev* __restrict__ wins, int w0, int spec_only)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const WinDev& W = wins[w0 + blockIdx.y];
     if (W.D != 3) return;
     const int M = W.M, b0 = W.box[0];
     const int MM = M * M;
-    const int c0 = blockIdx.x * 32;
+    const int c0 = blockIdx.x * kTile;
     if (c0 >= MM) return;
+    constexpr int JP = kTile / 2;                               // column pairs per tile
     float2* tx = reinterpret_cast<float2*>(smem);
     float2* ts = tx + b0 * M;
-    float4* ss = reinterpret_cast<float4*>(ts + b0 * 32);
-    const int cols = min(32, MM - c0);                          // M^2 need not be a multiple of 32
+    float4* ss = reinterpret_cast<float4*>(ts + b0 * kTile);
+    const int cols = min(kTile, MM - c0);                       // M^2 need not be a multiple of kTile
     const int r = blockIdx.z;                                  // right-hand-side slot
     const float2* t = reinterpret_cast<const float2*>(W.buf1 + r * W.b1sz);
-    for (int i = threadIdx.x; i < b0 * 32; i += kT)
-        ts[i] = (i & 31) < cols ? t[(size_t)(i >> 5) * MM + c0 + (i & 31)] : make_float2(0.f, 0.f);
-    for (int i = threadIdx.x; i < b0 * M; i += kT) tx[i] = W.twf[0][i];
+    for (int i = threadIdx.x; i < b0 * M; i += kT3) cp_async8(tx + i, W.twf[0] + i);
+    grid_dep_wait();
+    for (int i = threadIdx.x; i < b0 * kTile; i += kT3) {
+        const int x = i / kTile, j = i % kTile;
+        if (j < cols) cp_async8(ts + i, t + (size_t)x * MM + c0 + j);
+        else ts[i] = make_float2(0.f, 0.f);
+    }
+    cp_async_wait_all();
     __syncthreads();
     const float* mK = spec_only ? W.dconv : W.bK;
     const float* mD = spec_only ? W.dconv : W.bD;
     const int Mh = M / 2;
-    for (int o = threadIdx.x; o < Mh * 16; o += kT) {            // 2x2 blocks (kx, j)
-        const int kx = 2 * (o / 16), j = 2 * (o % 16);
+    for (int o = threadIdx.x; o < Mh * JP; o += kT3) {            // 2x2 blocks (kx, j)
+        const int kx = 2 * (o / JP), j = 2 * (o % JP);
         float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
 #pragma unroll 4
         for (int x = 0; x < b0; ++x) {
             const float4 w = *reinterpret_cast<const float4*>(tx + x * M + kx);
-            const float4 v = *reinterpret_cast<const float4*>(ts + x * 32 + j);
+            const float4 v = *reinterpret_cast<const float4*>(ts + x * kTile + j);
             const float2 w0 = make_float2(w.x, w.y), w1 = make_float2(w.z, w.w);
             const float2 s0 = make_float2(v.x, v.y), s1 = make_float2(v.z, v.w);
             a00 = cmad(s0, w0, a00);
@@ -149,27 +183,27 @@ __global__ void __launch_bounds__(kT) k_xround(const WinDev* __restrict__ wins, 
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 if (j + q >= cols) {
-                    if (!spec_only) ss[(kx + rr) * 32 + j + q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (!spec_only) ss[(kx + rr) * kTile + j + q] = make_float4(0.f, 0.f, 0.f, 0.f);
                     continue;
                 }
                 const size_t k = (size_t)(kx + rr) * MM + c0 + j + q;
                 const float a = __ldg(mK + k), d = __ldg(mD + k);
                 const float4 v = make_float4(a * acc[rr][q].x, a * acc[rr][q].y, d * acc[rr][q].x, d * acc[rr][q].y);
                 if (spec_only) W.spec[k] = v;
-                else ss[(kx + rr) * 32 + j + q] = v;
+                else ss[(kx + rr) * kTile + j + q] = v;
             }
     }
     if (spec_only) return;
     __syncthreads();
     const int nbx = (b0 + 1) / 2;
-    for (int o = threadIdx.x; o < nbx * 16; o += kT) {           // 2x2 blocks (x, j)
-        const int x0 = 2 * (o / 16), x1 = min(x0 + 1, b0 - 1), j = 2 * (o % 16);
+    for (int o = threadIdx.x; o < nbx * JP; o += kT3) {           // 2x2 blocks (x, j)
+        const int x0 = 2 * (o / JP), x1 = min(x0 + 1, b0 - 1), j = 2 * (o % JP);
         float2 k00 = make_float2(0.f, 0.f), k01 = k00, k10 = k00, k11 = k00;
         float2 d00 = k00, d01 = k00, d10 = k00, d11 = k00;
 #pragma unroll 4
         for (int kx = 0; kx < M; ++kx) {
             const float2 w0 = tx[x0 * M + kx], w1 = tx[x1 * M + kx];
-            const float4 s0 = ss[kx * 32 + j], s1 = ss[kx * 32 + j + 1];
+            const float4 s0 = ss[kx * kTile + j], s1 = ss[kx * kTile + j + 1];
             k00 = cmadc(make_float2(s0.x, s0.y), w0, k00);
             d00 = cmadc(make_float2(s0.z, s0.w), w0, d00);
             k01 = cmadc(make_float2(s1.x, s1.y), w0, k01);
@@ -191,36 +225,49 @@ __global__ void __launch_bounds__(kT) k_xround(const WinDev* __restrict__ wins, 
     }
 }
 
-// block = (x, window). smem: ty[b1][M], tz[b2][M] float2, bs[M][M] float4, b1s[b1][M] float4.
+// block = (x-slab and y part, window, rhs). smem: bs[M][M] float4, b1s[ny][M] float4, ty[ny][M],
+// tz[b2][M] float2, for the block's rows y = yb .. yb + ny - 1 (the last row repeated when b1 is odd):
 //   B1[y][kz] = sum_ky conj(ty[y][ky]) B[x][ky][kz];   h[x][y][z] = Re sum_kz conj(tz[z][kz]) B1[y][kz]
-__global__ void __launch_bounds__(kT) k_inv_yz(const WinDev* __restrict__ wins, int w0)
+// The block also zeroes its rows of the spread grid, which k_fwd_yz has consumed, so d = 3 grids
+// need no separate clearing before the next spread.
+__global__ void __launch_bounds__(kT3) k_inv_yz(const WinDev* __restrict__ wins, int w0)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const WinDev& W = wins[w0 + blockIdx.y];
     if (W.D != 3) return;
-    const int x = blockIdx.x;
+    const int x = blockIdx.x / kSplit, part = blockIdx.x % kSplit;
     const int b0 = W.box[0], b1 = W.box[1], b2 = W.box[2], M = W.M;
     if (x >= b0) return;
+    const int nb1 = (b1 + 1) / 2;
+    int q0, q1;
+    part_range(nb1, part, &q0, &q1);
+    const int nq = q1 - q0;
+    if (nq <= 0) return;
+    const int yb = 2 * q0, ny = 2 * nq;                         // local rows; global y = yb + local
     const int MM = M * M;
     float4* bs = reinterpret_cast<float4*>(smem);
     float4* b1s = bs + MM;
-    float2* ty = reinterpret_cast<float2*>(b1s + b1 * M);
-    float2* tz = ty + b1 * M;
+    float2* ty = reinterpret_cast<float2*>(b1s + ny * M);
+    float2* tz = ty + ny * M;
     const int r = blockIdx.z;                                  // right-hand-side slot
     const float4* B = W.buf2 + r * W.b2sz + (size_t)x * MM;
-    for (int i = threadIdx.x; i < MM; i += kT) bs[i] = B[i];
-    for (int i = threadIdx.x; i < b1 * M; i += kT) ty[i] = W.twf[1][i];
-    for (int i = threadIdx.x; i < b2 * M; i += kT) tz[i] = W.twf[2][i];
+    for (int i = threadIdx.x; i < ny * M; i += kT3) cp_async8(ty + i, W.twf[1] + min(yb + i / M, b1 - 1) * M + i % M);
+    for (int i = threadIdx.x; i < b2 * M; i += kT3) cp_async8(tz + i, W.twf[2] + i);
+    grid_dep_wait();
+    for (int i = threadIdx.x; i < MM; i += kT3) cp_async16(bs + i, B + i);
+    float* g = W.grid + r * W.gsz + (size_t)x * b1 * b2 + (size_t)yb * b2;
+    const int zrows = min(ny, b1 - yb);
+    for (int i = threadIdx.x; i < zrows * b2; i += kT3) g[i] = 0.f;
+    cp_async_wait_all();
     __syncthreads();
     const int Mh = M / 2;
-    const int nb1 = (b1 + 1) / 2;
-    for (int o = threadIdx.x; o < nb1 * Mh; o += kT) {           // 2x2 blocks (y, kz)
-        const int y0 = 2 * (o / Mh), y1 = min(y0 + 1, b1 - 1), kz = 2 * (o % Mh);
+    for (int o = threadIdx.x; o < nq * Mh; o += kT3) {            // 2x2 blocks (y, kz), local rows
+        const int y0 = 2 * (o / Mh), kz = 2 * (o % Mh);
         float2 k00 = make_float2(0.f, 0.f), k01 = k00, k10 = k00, k11 = k00;
         float2 d00 = k00, d01 = k00, d10 = k00, d11 = k00;
 #pragma unroll 4
         for (int ky = 0; ky < M; ++ky) {
-            const float2 w0 = ty[y0 * M + ky], w1 = ty[y1 * M + ky];
+            const float2 w0 = ty[y0 * M + ky], w1 = ty[(y0 + 1) * M + ky];
             const float4 s0 = bs[ky * M + kz], s1 = bs[ky * M + kz + 1];
             k00 = cmadc(make_float2(s0.x, s0.y), w0, k00);
             d00 = cmadc(make_float2(s0.z, s0.w), w0, d00);
@@ -233,22 +280,20 @@ __global__ void __launch_bounds__(kT) k_inv_yz(const WinDev* __restrict__ wins, 
         }
         b1s[y0 * M + kz] = make_float4(k00.x, k00.y, d00.x, d00.y);
         b1s[y0 * M + kz + 1] = make_float4(k01.x, k01.y, d01.x, d01.y);
-        if (y0 + 1 < b1) {
-            b1s[y1 * M + kz] = make_float4(k10.x, k10.y, d10.x, d10.y);
-            b1s[y1 * M + kz + 1] = make_float4(k11.x, k11.y, d11.x, d11.y);
-        }
+        b1s[(y0 + 1) * M + kz] = make_float4(k10.x, k10.y, d10.x, d10.y);
+        b1s[(y0 + 1) * M + kz + 1] = make_float4(k11.x, k11.y, d11.x, d11.y);
     }
     __syncthreads();
     float2* h = W.h + r * W.gsz + (size_t)x * b1 * b2;
     const int nb2 = (b2 + 1) / 2;
-    for (int o = threadIdx.x; o < nb1 * nb2; o += kT) {          // 2x2 blocks (y, z)
-        const int y0 = 2 * (o / nb2), y1 = min(y0 + 1, b1 - 1);
+    for (int o = threadIdx.x; o < nq * nb2; o += kT3) {          // 2x2 blocks (y, z), local rows
+        const int l0 = 2 * (o / nb2);
         const int z0 = 2 * (o % nb2), z1 = min(z0 + 1, b2 - 1);
         float k00 = 0.f, k01 = 0.f, k10 = 0.f, k11 = 0.f, d00 = 0.f, d01 = 0.f, d10 = 0.f, d11 = 0.f;
 #pragma unroll 4
         for (int kz = 0; kz < M; ++kz) {
             const float2 w0 = tz[z0 * M + kz], w1 = tz[z1 * M + kz];
-            const float4 s0 = b1s[y0 * M + kz], s1 = b1s[y1 * M + kz];
+            const float4 s0 = b1s[l0 * M + kz], s1 = b1s[(l0 + 1) * M + kz];
             // Re(s conj(w)) = s.re w.re + s.im w.im
             k00 = fmaf(s0.x, w0.x, fmaf(s0.y, w0.y, k00));
             d00 = fmaf(s0.z, w0.x, fmaf(s0.w, w0.y, d00));
@@ -259,9 +304,10 @@ __global__ void __launch_bounds__(kT) k_inv_yz(const WinDev* __restrict__ wins, 
             k11 = fmaf(s1.x, w1.x, fmaf(s1.y, w1.y, k11));
             d11 = fmaf(s1.z, w1.x, fmaf(s1.w, w1.y, d11));
         }
+        const int y0 = yb + l0, y1 = y0 + 1;
         h[y0 * b2 + z0] = make_float2(k00, d00);
         if (z0 + 1 < b2) h[y0 * b2 + z1] = make_float2(k01, d01);
-        if (y0 + 1 < b1) {
+        if (y1 < b1) {
             h[y1 * b2 + z0] = make_float2(k10, d10);
             if (z0 + 1 < b2) h[y1 * b2 + z1] = make_float2(k11, d11);
         }
@@ -304,10 +350,10 @@ __global__ void __launch_bounds__(kT) k_small_transform(const WinDev* __restrict
     float2* G = t + (D == 2 ? b0 * M : 0);                                       // MD
     float4* B = reinterpret_cast<float4*>(smem);                                 // b0 * M (D = 2)
     float4* S = reinterpret_cast<float4*>(smem + small_front(b0, b1, M, D));     // MD
-    for (int i = threadIdx.x; i < b0 * b1; i += kT) {
-        gs[i] = grid[i];
-        grid[i] = 0.f;
-    }
+    grid_dep_wait();
+    for (int i = threadIdx.x; i < b0 * b1; i += kT) cp_async4(gs + i, grid + i);
+    cp_async_wait_all();
+    for (int i = threadIdx.x; i < b0 * b1; i += kT) grid[i] = 0.f;     // each thread clears what it copied
     __syncthreads();
     if (D == 1) {
         for (int k = threadIdx.x; k < M; k += kT) {
@@ -397,20 +443,19 @@ size_t small_smem(const WinDev& w)
 }  // namespace
 
 // Shared memory of the fused D = 3 kernels for the largest box of the windows in range.
-static void fused_smem(const Plan& p, int lo, int hi, size_t* s1, size_t* s2, size_t* s3, int* maxb0, int* maxMM)
+static void fused_smem(const Plan& p, int lo, int hi, size_t* sm, int* maxb0, int* maxMM)
 {
-    *s1 = *s2 = *s3 = 0;
+    sm[0] = sm[1] = sm[2] = 0;
     *maxb0 = 0;
     *maxMM = 0;
     for (int s = lo; s < hi; ++s) {
         const WinDev& w = p.win[s];
         if (w.D != 3) continue;
-        const int b0 = w.box[0], b1 = w.box[1], b2 = w.box[2], M = w.M;
-        *s1 = std::max(*s1, sizeof(float2) * (b2 * M + 2 * b1 * M) + sizeof(float) * b1 * b2);
-        *s2 = std::max(*s2, sizeof(float2) * (b0 * M + b0 * 32) + sizeof(float4) * M * 32);
-        *s3 = std::max(*s3, sizeof(float4) * (M * M + b1 * M) + sizeof(float2) * (b1 + b2) * M);
-        *maxb0 = std::max(*maxb0, b0);
-        *maxMM = std::max(*maxMM, M * M);
+        size_t t[3];
+        fused3_smem(w.box[0], w.box[1], w.box[2], w.M, t);
+        for (int q = 0; q < 3; ++q) sm[q] = std::max(sm[q], t[q]);
+        *maxb0 = std::max(*maxb0, w.box[0]);
+        *maxMM = std::max(*maxMM, w.M * w.M);
     }
 }
 
@@ -433,25 +478,29 @@ cudaError_t launch_transforms(const Plan& p, int window, int nrhs, cudaStream_t 
     const int lo = window < 0 ? 0 : window, hi = window < 0 ? p.P : window + 1;
     if (spec_only) nrhs = 1;
     int n = 0;
-    size_t s1, s2, s3;
+    size_t f3[3];
     int maxb0, maxMM;
-    fused_smem(p, lo, hi, &s1, &s2, &s3, &maxb0, &maxMM);
+    fused_smem(p, lo, hi, f3, &maxb0, &maxMM);
     ensure_attrs();
     if (maxb0 > 0) {
-        dim3 g1(maxb0, hi - lo, nrhs), g2((maxMM + 31) / 32, hi - lo, nrhs);
-        k_fwd_yz<<<g1, kT, s1, st>>>(p.wins_dev, lo);
-        k_xround<<<g2, kT, s2, st>>>(p.wins_dev, lo, spec_only ? 1 : 0);
+        dim3 g1(maxb0 * kSplit, hi - lo, nrhs), g2((maxMM + kTile - 1) / kTile, hi - lo, nrhs);
+        launch_k(true, k_fwd_yz, g1, dim3(kT3), f3[0], st, (const WinDev*)p.wins_dev, lo);
+        launch_k(true, k_xround, g2, dim3(kT3), f3[1], st, (const WinDev*)p.wins_dev, lo, spec_only ? 1 : 0);
         n += 2;
         if (!spec_only) {
-            k_inv_yz<<<g1, kT, s3, st>>>(p.wins_dev, lo);
+            launch_k(true, k_inv_yz, g1, dim3(kT3), f3[2], st, (const WinDev*)p.wins_dev, lo);
             ++n;
         }
     }
     size_t sm[3] = {0, 0, 0};
     for (int s = lo; s < hi; ++s)
         if (p.win[s].D < 3) sm[p.win[s].D] = std::max(sm[p.win[s].D], small_smem(p.win[s]));
-    if (sm[1] > 0) { k_small_transform<1><<<dim3(hi - lo, nrhs), kT, sm[1], st>>>(p.wins_dev, lo, spec_only ? 1 : 0); ++n; }
-    if (sm[2] > 0) { k_small_transform<2><<<dim3(hi - lo, nrhs), kT, sm[2], st>>>(p.wins_dev, lo, spec_only ? 1 : 0); ++n; }
+    for (int D = 1; D <= 2; ++D) {
+        if (sm[D] == 0) continue;
+        launch_k(true, D == 1 ? k_small_transform<1> : k_small_transform<2>, dim3(hi - lo, nrhs), dim3(kT), sm[D],
+                 st, (const WinDev*)p.wins_dev, lo, spec_only ? 1 : 0);
+        ++n;
+    }
     if (count) *count = n;
     return cudaGetLastError();
 }
@@ -462,14 +511,12 @@ cudaError_t launch_transforms_window(const WinDev& w, const WinDev* w_dev, cudaS
 {
     ensure_attrs();
     if (w.D == 3) {
-        const int b0 = w.box[0], b1 = w.box[1], b2 = w.box[2], M = w.M;
-        const size_t s1 = sizeof(float2) * (b2 * M + 2 * b1 * M) + sizeof(float) * b1 * b2;
-        const size_t s2 = sizeof(float2) * (b0 * M + b0 * 32) + sizeof(float4) * M * 32;
-        const size_t s3 = sizeof(float4) * (M * M + b1 * M) + sizeof(float2) * (b1 + b2) * M;
-        dim3 g1(b0, 1, 1), g2((M * M + 31) / 32, 1, 1);
-        k_fwd_yz<<<g1, kT, s1, st>>>(w_dev, 0);
-        k_xround<<<g2, kT, s2, st>>>(w_dev, 0, 0);
-        k_inv_yz<<<g1, kT, s3, st>>>(w_dev, 0);
+        size_t f3[3];
+        fused3_smem(w.box[0], w.box[1], w.box[2], w.M, f3);
+        dim3 g1(w.box[0] * kSplit, 1, 1), g2((w.M * w.M + kTile - 1) / kTile, 1, 1);
+        k_fwd_yz<<<g1, kT3, f3[0], st>>>(w_dev, 0);
+        k_xround<<<g2, kT3, f3[1], st>>>(w_dev, 0, 0);
+        k_inv_yz<<<g1, kT3, f3[2], st>>>(w_dev, 0);
     } else if (w.D == 2) {
         k_small_transform<2><<<dim3(1, 1), kT, small_smem(w), st>>>(w_dev, 0, 0);
     } else {

@@ -96,11 +96,9 @@ int launch_pass(const Plan& p, const int4* items, int n, int D, const float* oth
 {
     const float sf2 = (float)(p.sigma_f * p.sigma_f);
     if (n == 0) return 0;
-    switch (D) {
-        case 1: k_gather_grad<1, PASS><<<n, 128, 0, st>>>(items, p.wins_dev, other, ks, grad_x, p.dots, p.P, p.d, p.N, sf2, p.poly); break;
-        case 2: k_gather_grad<2, PASS><<<n, 128, 0, st>>>(items, p.wins_dev, other, ks, grad_x, p.dots, p.P, p.d, p.N, sf2, p.poly); break;
-        default: k_gather_grad<3, PASS><<<n, 128, 0, st>>>(items, p.wins_dev, other, ks, grad_x, p.dots, p.P, p.d, p.N, sf2, p.poly); break;
-    }
+    auto kern = D == 1 ? k_gather_grad<1, PASS> : D == 2 ? k_gather_grad<2, PASS> : k_gather_grad<3, PASS>;
+    launch_k(false, kern, dim3(n), dim3(128), 0, st, items, (const WinDev*)p.wins_dev, other, ks, grad_x, p.dots,
+             p.P, p.d, p.N, sf2, p.poly);
     return 1;
 }
 

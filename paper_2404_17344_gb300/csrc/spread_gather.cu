@@ -527,13 +527,15 @@ cudaError_t launch_spread(const Plan& p, int window, const float* v, int64_t ldv
         const int n = hi - lo;
         const int4* it = p.items + lo;
         const dim3 warps((n + kWarps - 1) / kWarps, nrhs), blocks(n, nrhs);
+        const bool pdl = false;                // the first kernel of a product follows arbitrary stream work
+        const dim3 T(kWarps * 32), T2(128);
         switch (k) {
-            case kKindFast3: k_spread3_w8<<<warps, kWarps * 32, 0, st>>>(it, n, wd, v, ldv, p.poly); break;
-            case kKindLow1: k_spread_lowd_w8<1><<<warps, kWarps * 32, 0, st>>>(it, n, wd, v, ldv, p.poly); break;
-            case kKindLow2: k_spread_lowd_w8<2><<<warps, kWarps * 32, 0, st>>>(it, n, wd, v, ldv, p.poly); break;
-            case kKindGen1: k_spread_generic<1><<<blocks, 128, 0, st>>>(it, wd, v, ldv, p.poly); break;
-            case kKindGen2: k_spread_generic<2><<<blocks, 128, 0, st>>>(it, wd, v, ldv, p.poly); break;
-            default: k_spread_generic<3><<<blocks, 128, 0, st>>>(it, wd, v, ldv, p.poly); break;
+            case kKindFast3: launch_k(pdl, k_spread3_w8, warps, T, 0, st, it, n, wd, v, ldv, p.poly); break;
+            case kKindLow1: launch_k(pdl, k_spread_lowd_w8<1>, warps, T, 0, st, it, n, wd, v, ldv, p.poly); break;
+            case kKindLow2: launch_k(pdl, k_spread_lowd_w8<2>, warps, T, 0, st, it, n, wd, v, ldv, p.poly); break;
+            case kKindGen1: launch_k(pdl, k_spread_generic<1>, blocks, T2, 0, st, it, wd, v, ldv, p.poly); break;
+            case kKindGen2: launch_k(pdl, k_spread_generic<2>, blocks, T2, 0, st, it, wd, v, ldv, p.poly); break;
+            default: launch_k(pdl, k_spread_generic<3>, blocks, T2, 0, st, it, wd, v, ldv, p.poly); break;
         }
         ++launched;
     }
@@ -554,26 +556,31 @@ static int gather_all(const Plan& p, int window, float* oK, int64_t zK, int64_t 
         const int n = hi - lo;
         const int4* it = p.items + lo;
         const dim3 warps((n + kWarps - 1) / kWarps, nrhs), blocks(n, nrhs);
+        const bool pdl = false;                // griddepcontrol.wait in every warp measured slower
+        const dim3 T(kWarps * 32), T2(128);
         switch (k) {
             case kKindFast3:
-                k_gather3_w8<WK, WD><<<warps, kWarps * 32, 0, st>>>(it, n, wd, oK, oD, sK, sD, zK, zD, rK, rD, p.poly);
+                launch_k(pdl, k_gather3_w8<WK, WD>, warps, T, 0, st, it, n, wd, oK, oD, sK, sD, zK, zD, rK, rD, p.poly);
                 break;
             case kKindLow1:
-                k_gather_lowd_w8<1, WK, WD><<<warps, kWarps * 32, 0, st>>>(it, n, wd, oK, oD, sK, sD, zK, zD, rK, rD,
-                                                                          p.poly);
+                launch_k(pdl, k_gather_lowd_w8<1, WK, WD>, warps, T, 0, st, it, n, wd, oK, oD, sK, sD, zK, zD, rK, rD,
+                         p.poly);
                 break;
             case kKindLow2:
-                k_gather_lowd_w8<2, WK, WD><<<warps, kWarps * 32, 0, st>>>(it, n, wd, oK, oD, sK, sD, zK, zD, rK, rD,
-                                                                          p.poly);
+                launch_k(pdl, k_gather_lowd_w8<2, WK, WD>, warps, T, 0, st, it, n, wd, oK, oD, sK, sD, zK, zD, rK, rD,
+                         p.poly);
                 break;
             case kKindGen1:
-                k_gather_generic<1, WK, WD><<<blocks, 128, 0, st>>>(it, wd, oK, oD, sK, sD, zK, zD, rK, rD, p.poly);
+                launch_k(pdl, k_gather_generic<1, WK, WD>, blocks, T2, 0, st, it, wd, oK, oD, sK, sD, zK, zD, rK, rD,
+                         p.poly);
                 break;
             case kKindGen2:
-                k_gather_generic<2, WK, WD><<<blocks, 128, 0, st>>>(it, wd, oK, oD, sK, sD, zK, zD, rK, rD, p.poly);
+                launch_k(pdl, k_gather_generic<2, WK, WD>, blocks, T2, 0, st, it, wd, oK, oD, sK, sD, zK, zD, rK, rD,
+                         p.poly);
                 break;
             default:
-                k_gather_generic<3, WK, WD><<<blocks, 128, 0, st>>>(it, wd, oK, oD, sK, sD, zK, zD, rK, rD, p.poly);
+                launch_k(pdl, k_gather_generic<3, WK, WD>, blocks, T2, 0, st, it, wd, oK, oD, sK, sD, zK, zD, rK, rD,
+                         p.poly);
                 break;
         }
         ++launched;
