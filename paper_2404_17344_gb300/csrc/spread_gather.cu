@@ -30,8 +30,12 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 
 // fast 3-D spread, m = 4 (W = 8)
 // Staged per point (STRIDE floats): xp[8] pairs (x_a v, x_a v) | wy[8] | zp[8] pairs (z_c, z_c).
-// Lane (ah, bh, c) accumulates acc[a][p] = (g[4ah+a][4bh+2p][c], g[4ah+a][4bh+2p+1][c]).
-__global__ void __launch_bounds__(kWarps * 32) k_spread3_w8(const int4* __restrict__ items, int nitems,
+// The two half-warps take alternate staged points (hw = lane >> 4). Within a half-warp, lane
+// (ah, bh, cq) accumulates acc[a][p][i] = (g[4ah+a][4bh+2p][2cq+i], g[4ah+a][4bh+2p+1][2cq+i]): the
+// whole box per half-warp, 32 values per lane, so each point costs a lane 4 shared loads (16 bytes
+// each), 4 packed products and 16 packed FMAs, and a shared load serves twice as many FMAs as with
+// one box per warp. The two halves are summed once per item, before the atomic adds.
+__global__ void __launch_bounds__(kWarps * 32, 2) k_spread3_w8(const int4* __restrict__ items, int nitems,
                                                            const WinDev* __restrict__ wins,
                                                            const float* __restrict__ v, int64_t ldv,
                                                            const WinPoly poly)
@@ -50,11 +54,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_spread3_w8(const int4* __restri
     v += r * ldv;
     const int n = P.n;
     float* ws = sw[warp];
-    const int ah = lane >> 4, bh = (lane >> 3) & 1, c = lane & 7;
+    const int hw = lane >> 4, ah = (lane >> 3) & 1, bh = (lane >> 2) & 1, cq = lane & 3;
 
-    float2 acc[4][2];
+    float2 acc[4][2][2];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) { acc[a][0] = f2(0.f, 0.f); acc[a][1] = f2(0.f, 0.f); }
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[a][q >> 1][q & 1] = f2(0.f, 0.f);
 
     // software pipeline: the next batch's point (and then its v) is in flight during this batch
     float4 pn = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -90,37 +96,52 @@ __global__ void __launch_bounds__(kWarps * 32) k_spread3_w8(const int4* __restri
 #pragma unroll
         for (int q = 0; q < W; q += 2) dst[6 + q / 2] = make_float4(wz[q], wz[q], wz[q + 1], wz[q + 1]);
         __syncwarp();
+        // rows cnt .. 31 hold zeros (lanes without a point stage zero weights), so an odd count is safe
         const int cnt = min(32, count - base);
-        const float* src = ws;
-#pragma unroll 4
-        for (int j = 0; j < cnt; ++j, src += STRIDE) {
+        const float* src = ws + hw * STRIDE;
+#pragma unroll 2
+        for (int j = 0; j < cnt; j += 2, src += 2 * STRIDE) {
             const float4 x01 = *reinterpret_cast<const float4*>(src + 8 * ah);        // a = 4ah, 4ah+1
             const float4 x23 = *reinterpret_cast<const float4*>(src + 8 * ah + 4);    // a = 4ah+2, 4ah+3
-            const float4 yb = *reinterpret_cast<const float4*>(src + 16 + 4 * bh);
-            const float2 zz = *reinterpret_cast<const float2*>(src + 24 + 2 * c);
-            const float2 B01 = __fmul2_rn(f2(yb.x, yb.y), zz);
-            const float2 B23 = __fmul2_rn(f2(yb.z, yb.w), zz);
+            const float4 yb = *reinterpret_cast<const float4*>(src + 16 + 4 * bh);    // b = 4bh .. 4bh+3
+            const float4 zz = *reinterpret_cast<const float4*>(src + 24 + 4 * cq);    // c = 2cq, 2cq+1 (pairs)
+            const float2 Y[2] = {f2(yb.x, yb.y), f2(yb.z, yb.w)};
+            const float2 Z[2] = {f2(zz.x, zz.y), f2(zz.z, zz.w)};
             const float2 X[4] = {f2(x01.x, x01.y), f2(x01.z, x01.w), f2(x23.x, x23.y), f2(x23.z, x23.w)};
+            float2 B[2][2];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                acc[a][0] = __ffma2_rn(X[a], B01, acc[a][0]);
-                acc[a][1] = __ffma2_rn(X[a], B23, acc[a][1]);
-            }
+            for (int q = 0; q < 4; ++q) B[q >> 1][q & 1] = __fmul2_rn(Y[q >> 1], Z[q & 1]);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    acc[a][q >> 1][q & 1] = __ffma2_rn(X[a], B[q >> 1][q & 1], acc[a][q >> 1][q & 1]);
         }
         __syncwarp();
     }
-    // flush: grid index of (a, b, c) relative to the box origin
+    // sum the halves: half hw keeps the values with i = hw and receives its partner's
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const float2 send = hw ? acc[a][p][0] : acc[a][p][1];
+            float2 keep = hw ? acc[a][p][1] : acc[a][p][0];
+            keep.x += __shfl_xor_sync(0xffffffffu, send.x, 16);
+            keep.y += __shfl_xor_sync(0xffffffffu, send.y, 16);
+            acc[a][p][0] = keep;
+        }
+    // flush: grid index of (a, b, c) relative to the box origin, c = 2cq + hw
     const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff, cz = (it.z >> 16) & 0xff;
     const int ox = cx - 3 - P.lo[0], oy = cy - 3 - P.lo[1], oz = cz - 3 - P.lo[2];
     const int sy = P.box[2], sx = P.box[1] * P.box[2];
-    float* g = P.grid + r * P.gsz + (size_t)(ox + 4 * ah) * sx + (size_t)(oy + 4 * bh) * sy + oz + c;
+    float* g = P.grid + r * P.gsz + (size_t)(ox + 4 * ah) * sx + (size_t)(oy + 4 * bh) * sy + oz + 2 * cq + hw;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         float* ga = g + (size_t)a * sx;
-        atomicAdd(ga, acc[a][0].x);
-        atomicAdd(ga + sy, acc[a][0].y);
-        atomicAdd(ga + 2 * sy, acc[a][1].x);
-        atomicAdd(ga + 3 * sy, acc[a][1].y);
+        atomicAdd(ga, acc[a][0][0].x);
+        atomicAdd(ga + sy, acc[a][0][0].y);
+        atomicAdd(ga + 2 * sy, acc[a][1][0].x);
+        atomicAdd(ga + 3 * sy, acc[a][1][0].y);
     }
 }
 
