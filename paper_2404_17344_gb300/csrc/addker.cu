@@ -1020,6 +1020,7 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
     if (status == ADDKER_OK) status = dalloc(p, &p.wins_dev, P);
     if (status == ADDKER_OK) status = dalloc(p, &p.scale_dev, 3 * P);
     if (status == ADDKER_OK) status = dalloc(p, &p.dots, 2 * P);
+    if (status == ADDKER_OK) status = dalloc(p, &p.counters, 16);
     for (int s = 0; s < P && status == ADDKER_OK; ++s) status = compute_multipliers(p, s);
     if (status == ADDKER_OK && cudaMemcpy(p.wins_dev, p.win.data(), sizeof(WinDev) * P, cudaMemcpyHostToDevice) != cudaSuccess)
         status = ADDKER_ECUDA;

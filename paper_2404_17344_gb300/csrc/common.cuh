@@ -103,6 +103,7 @@ struct Plan {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
     int64_t launches[5] = {0, 0, 0, 0, 0};
     double* dots = nullptr;               // 2P doubles: gradient dot products (addker_vjp)
+    int* counters = nullptr;              // work counters of the persistent kernels (zeroed per launch)
 };
 
 // Launch a kernel on st. With pdl the launch carries the programmatic-serialisation attribute (the

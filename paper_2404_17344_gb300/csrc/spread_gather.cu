@@ -15,6 +15,9 @@
 //   gather: a warp stages the item's box of both grids in shared memory (float2 (h^K, h^der)) and
 //           every lane contracts it with two points at once, the grid pair in one packed FMA, so
 //           one 16-byte broadcast load feeds 8 FMAs in 4 instructions.
+#include <map>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace addker {
@@ -35,113 +38,140 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // whole box per half-warp, 32 values per lane, so each point costs a lane 4 shared loads (16 bytes
 // each), 4 packed products and 16 packed FMAs, and a shared load serves twice as many FMAs as with
 // one box per warp. The two halves are summed once per item, before the atomic adds.
+//
+// Persistent: each warp takes work units (item, right-hand side) from a global counter, one unit
+// ahead, and loads the first batch of the next unit while it finishes the current one, so neither
+// the chain item -> points -> v at the start of an item nor the drain of the atomic adds at its end
+// stalls the warp. Unit u is item u % nitems of right-hand side u / nitems.
 __global__ void __launch_bounds__(kWarps * 32, 2) k_spread3_w8(const int4* __restrict__ items, int nitems,
-                                                           const WinDev* __restrict__ wins,
-                                                           const float* __restrict__ v, int64_t ldv,
-                                                           const WinPoly poly)
+                                                              int nunits, int* __restrict__ counter,
+                                                              const WinDev* __restrict__ wins,
+                                                              const float* __restrict__ v, int64_t ldv,
+                                                              const WinPoly poly)
 {
     constexpr int W = 8;
     constexpr int STRIDE = 44;            // 16 + 8 + 16 floats, padded so staging stores avoid conflicts
     __shared__ __align__(16) float sw[kWarps][32 * STRIDE];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int item = blockIdx.x * kWarps + warp;
-    if (item >= nitems) return;
-    const int4 it = items[item];
-    const WinDev& P = wins[it.w];
-    const float4* __restrict__ pts = P.pts + it.x;
-    const int count = it.y;
-    const int r = blockIdx.y;                                  // right-hand side
-    v += r * ldv;
-    const int n = P.n;
     float* ws = sw[warp];
     const int hw = lane >> 4, ah = (lane >> 3) & 1, bh = (lane >> 2) & 1, cq = lane & 3;
 
-    float2 acc[4][2][2];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[a][q >> 1][q & 1] = f2(0.f, 0.f);
-
+    int u = 0;
+    if (lane == 0) u = atomicAdd(counter, 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= nunits) return;
+    int un = 0;
+    if (lane == 0) un = atomicAdd(counter, 1);
+    un = __shfl_sync(0xffffffffu, un, 0);
+    int4 it = items[u % nitems];
+    int r = u / nitems;
+    int4 itn = un < nunits ? items[un % nitems] : make_int4(0, 0, 0, 0);
+    const WinDev* P = wins + it.w;
+    const float4* __restrict__ pts = P->pts + it.x;
+    const float* __restrict__ vr = v + r * ldv;
     // software pipeline: the next batch's point (and then its v) is in flight during this batch
     float4 pn = make_float4(0.f, 0.f, 0.f, 0.f);
     float vn = 0.f;
-    if (lane < count) {
+    if (lane < it.y) {
         pn = pts[lane];
-        vn = __ldg(v + __float_as_int(pn.w));
+        vn = __ldg(vr + __float_as_int(pn.w));
     }
-    for (int base = 0; base < count; base += 32) {
-        const float4 p = pn;
-        const float vv = vn;
-        const bool valid = base + lane < count;
-        const int kn = base + 32 + lane;
-        if (kn < count) pn = pts[kn];
-        float wx[W], wy[W], wz[W];
-        int cx, cy, cz;
-        if (valid) {
-            window_weights<W>(poly, p.x, n, wx, &cx);
-            window_weights<W>(poly, p.y, n, wy, &cy);
-            window_weights<W>(poly, p.z, n, wz, &cz);
+    while (true) {
+        float2 acc[4][2][2];
 #pragma unroll
-            for (int q = 0; q < W; ++q) wx[q] *= vv;
-        } else {
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int q = 0; q < W; ++q) { wx[q] = 0.f; wy[q] = 0.f; wz[q] = 0.f; }
-        }
-        if (kn < count) vn = __ldg(v + __float_as_int(pn.w));
-        float4* dst = reinterpret_cast<float4*>(ws + lane * STRIDE);
+            for (int q = 0; q < 4; ++q) acc[a][q >> 1][q & 1] = f2(0.f, 0.f);
+        const int count = it.y;
+        const int n = P->n;
+        const bool more = un < nunits;
+        for (int base = 0; base < count; base += 32) {
+            const float4 p = pn;
+            const float vv = vn;
+            const bool valid = base + lane < count;
+            const bool last = base + 32 >= count;
+            // prefetch: the next batch of this item, or the first batch of the next unit
+            const float4* __restrict__ npts = last ? wins[itn.w].pts + itn.x : pts + base + 32;
+            const int ncount = last ? (more ? itn.y : 0) : count - base - 32;
+            if (lane < ncount) pn = npts[lane];
+            float wx[W], wy[W], wz[W];
+            int cx, cy, cz;
+            if (valid) {
+                window_weights<W>(poly, p.x, n, wx, &cx);
+                window_weights<W>(poly, p.y, n, wy, &cy);
+                window_weights<W>(poly, p.z, n, wz, &cz);
 #pragma unroll
-        for (int q = 0; q < W; q += 2) dst[q / 2] = make_float4(wx[q], wx[q], wx[q + 1], wx[q + 1]);
-        dst[4] = make_float4(wy[0], wy[1], wy[2], wy[3]);
-        dst[5] = make_float4(wy[4], wy[5], wy[6], wy[7]);
+                for (int q = 0; q < W; ++q) wx[q] *= vv;
+            } else {
 #pragma unroll
-        for (int q = 0; q < W; q += 2) dst[6 + q / 2] = make_float4(wz[q], wz[q], wz[q + 1], wz[q + 1]);
-        __syncwarp();
-        // rows cnt .. 31 hold zeros (lanes without a point stage zero weights), so an odd count is safe
-        const int cnt = min(32, count - base);
-        const float* src = ws + hw * STRIDE;
+                for (int q = 0; q < W; ++q) { wx[q] = 0.f; wy[q] = 0.f; wz[q] = 0.f; }
+            }
+            if (lane < ncount) vn = __ldg((last ? v + (un / nitems) * ldv : vr) + __float_as_int(pn.w));
+            float4* dst = reinterpret_cast<float4*>(ws + lane * STRIDE);
+#pragma unroll
+            for (int q = 0; q < W; q += 2) dst[q / 2] = make_float4(wx[q], wx[q], wx[q + 1], wx[q + 1]);
+            dst[4] = make_float4(wy[0], wy[1], wy[2], wy[3]);
+            dst[5] = make_float4(wy[4], wy[5], wy[6], wy[7]);
+#pragma unroll
+            for (int q = 0; q < W; q += 2) dst[6 + q / 2] = make_float4(wz[q], wz[q], wz[q + 1], wz[q + 1]);
+            __syncwarp();
+            // rows cnt .. 31 hold zeros (lanes without a point stage zero weights), so an odd count is safe
+            const int cnt = min(32, count - base);
+            const float* src = ws + hw * STRIDE;
 #pragma unroll 2
-        for (int j = 0; j < cnt; j += 2, src += 2 * STRIDE) {
-            const float4 x01 = *reinterpret_cast<const float4*>(src + 8 * ah);        // a = 4ah, 4ah+1
-            const float4 x23 = *reinterpret_cast<const float4*>(src + 8 * ah + 4);    // a = 4ah+2, 4ah+3
-            const float4 yb = *reinterpret_cast<const float4*>(src + 16 + 4 * bh);    // b = 4bh .. 4bh+3
-            const float4 zz = *reinterpret_cast<const float4*>(src + 24 + 4 * cq);    // c = 2cq, 2cq+1 (pairs)
-            const float2 Y[2] = {f2(yb.x, yb.y), f2(yb.z, yb.w)};
-            const float2 Z[2] = {f2(zz.x, zz.y), f2(zz.z, zz.w)};
-            const float2 X[4] = {f2(x01.x, x01.y), f2(x01.z, x01.w), f2(x23.x, x23.y), f2(x23.z, x23.w)};
-            float2 B[2][2];
+            for (int j = 0; j < cnt; j += 2, src += 2 * STRIDE) {
+                const float4 x01 = *reinterpret_cast<const float4*>(src + 8 * ah);        // a = 4ah, 4ah+1
+                const float4 x23 = *reinterpret_cast<const float4*>(src + 8 * ah + 4);    // a = 4ah+2, 4ah+3
+                const float4 yb = *reinterpret_cast<const float4*>(src + 16 + 4 * bh);    // b = 4bh .. 4bh+3
+                const float4 zz = *reinterpret_cast<const float4*>(src + 24 + 4 * cq);    // c = 2cq, 2cq+1 (pairs)
+                const float2 Y[2] = {f2(yb.x, yb.y), f2(yb.z, yb.w)};
+                const float2 Z[2] = {f2(zz.x, zz.y), f2(zz.z, zz.w)};
+                const float2 X[4] = {f2(x01.x, x01.y), f2(x01.z, x01.w), f2(x23.x, x23.y), f2(x23.z, x23.w)};
+                float2 B[2][2];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) B[q >> 1][q & 1] = __fmul2_rn(Y[q >> 1], Z[q & 1]);
+                for (int q = 0; q < 4; ++q) B[q >> 1][q & 1] = __fmul2_rn(Y[q >> 1], Z[q & 1]);
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+                for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    acc[a][q >> 1][q & 1] = __ffma2_rn(X[a], B[q >> 1][q & 1], acc[a][q >> 1][q & 1]);
+                    for (int q = 0; q < 4; ++q)
+                        acc[a][q >> 1][q & 1] = __ffma2_rn(X[a], B[q >> 1][q & 1], acc[a][q >> 1][q & 1]);
+            }
+            __syncwarp();
         }
-        __syncwarp();
-    }
-    // sum the halves: half hw keeps the values with i = hw and receives its partner's
+        // sum the halves: half hw keeps the values with i = hw and receives its partner's
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            const float2 send = hw ? acc[a][p][0] : acc[a][p][1];
-            float2 keep = hw ? acc[a][p][1] : acc[a][p][0];
-            keep.x += __shfl_xor_sync(0xffffffffu, send.x, 16);
-            keep.y += __shfl_xor_sync(0xffffffffu, send.y, 16);
-            acc[a][p][0] = keep;
+            for (int p = 0; p < 2; ++p) {
+                const float2 send = hw ? acc[a][p][0] : acc[a][p][1];
+                float2 keep = hw ? acc[a][p][1] : acc[a][p][0];
+                keep.x += __shfl_xor_sync(0xffffffffu, send.x, 16);
+                keep.y += __shfl_xor_sync(0xffffffffu, send.y, 16);
+                acc[a][p][0] = keep;
+            }
+        // flush: grid index of (a, b, c) relative to the box origin, c = 2cq + hw
+        const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff, cz = (it.z >> 16) & 0xff;
+        const int ox = cx - 3 - P->lo[0], oy = cy - 3 - P->lo[1], oz = cz - 3 - P->lo[2];
+        const int sy = P->box[2], sx = P->box[1] * P->box[2];
+        float* g = P->grid + r * P->gsz + (size_t)(ox + 4 * ah) * sx + (size_t)(oy + 4 * bh) * sy + oz + 2 * cq + hw;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            float* ga = g + (size_t)a * sx;
+            atomicAdd(ga, acc[a][0][0].x);
+            atomicAdd(ga + sy, acc[a][0][0].y);
+            atomicAdd(ga + 2 * sy, acc[a][1][0].x);
+            atomicAdd(ga + 3 * sy, acc[a][1][0].y);
         }
-    // flush: grid index of (a, b, c) relative to the box origin, c = 2cq + hw
-    const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff, cz = (it.z >> 16) & 0xff;
-    const int ox = cx - 3 - P.lo[0], oy = cy - 3 - P.lo[1], oz = cz - 3 - P.lo[2];
-    const int sy = P.box[2], sx = P.box[1] * P.box[2];
-    float* g = P.grid + r * P.gsz + (size_t)(ox + 4 * ah) * sx + (size_t)(oy + 4 * bh) * sy + oz + 2 * cq + hw;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        float* ga = g + (size_t)a * sx;
-        atomicAdd(ga, acc[a][0][0].x);
-        atomicAdd(ga + sy, acc[a][0][0].y);
-        atomicAdd(ga + 2 * sy, acc[a][1][0].x);
-        atomicAdd(ga + 3 * sy, acc[a][1][0].y);
+        if (!more) break;
+        // advance: the prefetched unit becomes current; take the one after it
+        it = itn;
+        r = un / nitems;
+        P = wins + it.w;
+        pts = P->pts + it.x;
+        vr = v + r * ldv;
+        if (lane == 0) un = atomicAdd(counter, 1);
+        un = __shfl_sync(0xffffffffu, un, 0);
+        itn = un < nunits ? items[un % nitems] : make_int4(0, 0, 0, 0);
     }
 }
 
@@ -527,6 +557,27 @@ __global__ void __launch_bounds__(128) k_gather_generic(const int4* __restrict__
 
 }  // namespace
 
+// Blocks of `kernel` (block threads, no dynamic shared memory) resident on the whole device at once,
+// cached per device and kernel.
+template <typename K>
+static int resident_blocks(K kernel, int threads)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_pair(dev, reinterpret_cast<const void*>(kernel));
+    std::lock_guard<std::mutex> lock(mu);
+    auto f = cache.find(key);
+    if (f != cache.end()) return f->second;
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0);
+    const int nb = std::max(1, sms * std::max(1, per));
+    cache[key] = nb;
+    return nb;
+}
+
 // Items of one kind for one window, or for all windows (window < 0).
 static void item_range(const Plan& p, int kind, int window, int* lo, int* hi)
 {
@@ -551,7 +602,14 @@ cudaError_t launch_spread(const Plan& p, int window, const float* v, int64_t ldv
         const bool pdl = false;                // the first kernel of a product follows arbitrary stream work
         const dim3 T(kWarps * 32), T2(128);
         switch (k) {
-            case kKindFast3: launch_k(pdl, k_spread3_w8, warps, T, 0, st, it, n, wd, v, ldv, p.poly); break;
+            case kKindFast3: {
+                // persistent: as many blocks as fit at once, units taken from a zeroed counter
+                const int units = n * nrhs;
+                const int nb = std::min(resident_blocks(k_spread3_w8, kWarps * 32), (units + kWarps - 1) / kWarps);
+                if (cudaMemsetAsync(p.counters, 0, sizeof(int), st) != cudaSuccess) return cudaGetLastError();
+                launch_k(pdl, k_spread3_w8, dim3(nb), T, 0, st, it, n, units, p.counters, wd, v, ldv, p.poly);
+                break;
+            }
             case kKindLow1: launch_k(pdl, k_spread_lowd_w8<1>, warps, T, 0, st, it, n, wd, v, ldv, p.poly); break;
             case kKindLow2: launch_k(pdl, k_spread_lowd_w8<2>, warps, T, 0, st, it, n, wd, v, ldv, p.poly); break;
             case kKindGen1: launch_k(pdl, k_spread_generic<1>, blocks, T2, 0, st, it, wd, v, ldv, p.poly); break;
