@@ -111,6 +111,18 @@ int addker_setup(addker_plan** plan, const float* points, int64_t N, int d,
  * sorted points are kept. ell may be NULL to keep the length scales. Synchronous. */
 int addker_set_params(addker_plan* plan, const double* ell, double sigma_f);
 
+/*
+ * CUDA graphs for repeated products (enable = 1, the default; 0 = every call launches its kernels).
+ * When a product entry point (addker_matvec, addker_dmatvec, addker_matvec_all and the host variant)
+ * is called twice in a row with the same pointers, nrhs and selector, the second call captures the
+ * product on a private stream and every later identical call replays it on the plan's stream. Graphs
+ * bake in pointers and sigma_f: addker_set_params, slot growth and this call discard them. No graph
+ * is used while stage profiling is on or while the plan's stream is itself being captured (the
+ * caller's capture then records the kernels). EINVAL for enable other than 0/1. Synchronises the
+ * plan's stream.
+ */
+int addker_set_graphs(addker_plan* plan, int enable);
+
 /* Set the CUDA stream (cudaStream_t, NULL = legacy default) used by later products. */
 int addker_set_stream(addker_plan* plan, void* stream);
 
@@ -192,7 +204,9 @@ int addker_prescale(const float* X, int64_t N, int d, const int* win_off, const 
 /*
  * Plan inspection for tests and benchmarks. Writes up to `cap` int64 values into info:
  *   [0] N  [1] P  [2] number of work items over all windows  [3] bytes of device memory owned
- *   then per window s: [4+4s] d_s  [5+4s] M_s  [6+4s] n_s  [7+4s] number of non-empty cells.
+ *   then per window s: [4+4s] d_s  [5+4s] M_s  [6+4s] n_s  [7+4s] number of non-empty cells,
+ *   then [4+4P] right-hand-side slots allocated  [5+4P] captured product graphs held
+ *   [6+4P] product graph replays so far.
  * Returns the number of values available.
  */
 int addker_info(const addker_plan* plan, int64_t* info, int cap);

@@ -91,12 +91,16 @@ class AddKer:
         return native.lib()
 
     def _rhs(self, v):
-        v = _dev_f32(v, "v")
+        torch = _torch()
+        if not (isinstance(v, torch.Tensor) and v.is_cuda and v.dtype == torch.float32):
+            raise TypeError("v must be a float32 CUDA tensor")
         if v.shape[0] != self.N or v.dim() not in (1, 2):
             raise ValueError("v must be (N,) or (N, nrhs) with column j a right-hand side")
         nrhs = 1 if v.dim() == 1 else int(v.shape[1])
         if v.dim() == 2:
-            v = v.t().contiguous()         # column-major (nrhs, N) storage
+            v = v.t()                      # column-major (nrhs, N) storage; a column-major view is not copied
+        if not v.is_contiguous():
+            v = v.contiguous()
         return v, nrhs
 
     @staticmethod
@@ -179,6 +183,10 @@ class AddKer:
             self.ell = [float(e) for e in ell]
         self.sigma_f = sf
 
+    def set_graphs(self, enable):
+        """Replay repeated identical products as CUDA graphs (default on); False launches every kernel."""
+        native.check(self._ready().addker_set_graphs(self._plan, 1 if enable else 0), "addker_set_graphs")
+
     STAGES = ("clear", "spread", "transform", "gather", "window_sum")
 
     def profile(self, enable=True):
@@ -198,13 +206,15 @@ class AddKer:
         native.check(native.lib().addker_sync(self._plan), "addker_sync")
 
     def info(self):
-        cap = 4 + 4 * self.P
+        cap = 7 + 4 * self.P
         buf = (ctypes.c_int64 * cap)()
         n = native.lib().addker_info(self._plan, buf, cap)
         vals = list(buf[:n])
+        e = 4 + 4 * self.P
         return {"N": vals[0], "P": vals[1], "items": vals[2], "device_bytes": vals[3],
                 "windows": [dict(d=vals[4 + 4 * s], M=vals[5 + 4 * s], n=vals[6 + 4 * s], cells=vals[7 + 4 * s])
-                            for s in range(self.P)]}
+                            for s in range(self.P)],
+                "slots": vals[e], "graphs": vals[e + 1], "graph_replays": vals[e + 2]}
 
     def debug_stage(self, window, stage, v):
         """Stage 0: spread grid (n^d doubles); stage 1: adjoint NFFT S_k (complex M^d). Synchronous."""

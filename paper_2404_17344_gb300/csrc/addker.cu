@@ -58,8 +58,19 @@ int dalloc(Plan& p, T** ptr, int64_t count)
     return ADDKER_OK;
 }
 
+// Forget every captured product (buffers, slots or scalars they bake in have changed).
+void clear_graphs(Plan& p)
+{
+    for (auto& e : p.graph_cache) cudaGraphExecDestroy(e.second);
+    p.graph_cache.clear();
+    p.last_key = {nullptr, nullptr, nullptr, 0, 0, -1};
+}
+
 void release(Plan& p)
 {
+    clear_graphs(p);
+    if (p.cap_stream) cudaStreamDestroy(p.cap_stream);
+    p.cap_stream = nullptr;
     for (void* a : p.allocations) cudaFree(a);
     p.allocations.clear();
     for (void* a : p.slot_allocs) cudaFree(a);
@@ -705,6 +716,7 @@ int ensure_slots(Plan& p, int want)
     while (r < want) r *= 2;
     r = std::min(r, kMaxRhsChunk);
     CK(cudaStreamSynchronize(p.stream));
+    clear_graphs(p);                               // captured products point at the old slots
     for (void* a : p.slot_allocs) cudaFree(a);
     p.slot_allocs.clear();
     p.bytes -= p.slot_bytes;
@@ -816,16 +828,67 @@ int product(Plan& p, const float* v, int64_t ldv, int R, float* Kv, int64_t ldk,
 }
 
 // nrhs right-hand sides (columns of length N, v + j N) in chunks of at most kMaxRhsChunk.
-int product_all(Plan& p, const float* v, int nrhs, float* Kv, float* dK, int window, int mode)
+int product_chunks(Plan& p, const float* v, int nrhs, float* Kv, float* dK, int window, int mode)
 {
-    // a batch that cannot get more slots runs in single-right-hand-side chunks
-    if (ensure_slots(p, nrhs) != ADDKER_OK) CS(ensure_slots(p, 1));
     const int64_t N = p.N;
     const int64_t ldd = mode == 0 ? N * p.P : N;
     for (int j = 0; j < nrhs; j += p.slots) {
         const int R = std::min(p.slots, nrhs - j);
         CS(product(p, v + j * N, N, R, Kv ? Kv + j * N : nullptr, N, dK ? dK + j * ldd : nullptr, ldd, window, mode));
     }
+    return ADDKER_OK;
+}
+
+// All products go through here. With graphs on (and no stage profiling, and a stream that is not itself
+// being captured), the second consecutive call with the same arguments is captured on a private stream
+// and every later one replays the graph on the plan's stream: one launch instead of one per kernel.
+int product_all(Plan& p, const float* v, int nrhs, float* Kv, float* dK, int window, int mode)
+{
+    // a batch that cannot get more slots runs in single-right-hand-side chunks
+    if (ensure_slots(p, nrhs) != ADDKER_OK) CS(ensure_slots(p, 1));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (!p.graphs || p.prof || cudaStreamIsCapturing(p.stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return product_chunks(p, v, nrhs, Kv, dK, window, mode);
+    }
+    const Plan::GraphKey key = {v, Kv, dK, nrhs, window, mode};
+    for (size_t i = 0; i < p.graph_cache.size(); ++i)
+        if (p.graph_cache[i].first == key) {
+            auto e = p.graph_cache[i];
+            p.graph_cache.erase(p.graph_cache.begin() + i);
+            p.graph_cache.push_back(e);
+            CK(cudaGraphLaunch(e.second, p.stream));
+            ++p.graph_replays;
+            return ADDKER_OK;
+        }
+    if (!(p.last_key == key)) {                    // first sighting: run eagerly, capture if it repeats
+        p.last_key = key;
+        return product_chunks(p, v, nrhs, Kv, dK, window, mode);
+    }
+    if (!p.cap_stream) CK(cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeThreadLocal));
+    const cudaStream_t user = p.stream;
+    p.stream = p.cap_stream;
+    const int status = product_chunks(p, v, nrhs, Kv, dK, window, mode);
+    p.stream = user;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(p.cap_stream, &graph);
+    if (status != ADDKER_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return status != ADDKER_OK ? status : ADDKER_ECUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ei);
+    constexpr size_t kMaxGraphs = 8;
+    if (p.graph_cache.size() >= kMaxGraphs) {
+        cudaGraphExecDestroy(p.graph_cache.front().second);
+        p.graph_cache.erase(p.graph_cache.begin());
+    }
+    p.graph_cache.push_back({key, exec});
+    CK(cudaGraphLaunch(exec, p.stream));
     return ADDKER_OK;
 }
 
@@ -1047,8 +1110,19 @@ int addker_set_params(addker_plan* plan, const double* ell, double sigma_f)
     }
     p.sigma_f = sigma_f;
     CK(cudaStreamSynchronize(p.stream));
+    clear_graphs(p);                               // sigma_f is baked into captured window sums
     for (int s = 0; s < p.P; ++s) CS(compute_multipliers(p, s));
     return upload_scales(p);
+}
+
+int addker_set_graphs(addker_plan* plan, int enable)
+{
+    if (!plan || (enable != 0 && enable != 1)) return ADDKER_EINVAL;
+    Plan& p = plan->p;
+    CK(cudaStreamSynchronize(p.stream));
+    clear_graphs(p);
+    p.graphs = enable == 1;
+    return ADDKER_OK;
 }
 
 int addker_set_stream(addker_plan* plan, void* stream)
@@ -1238,6 +1312,9 @@ int addker_info(const addker_plan* plan, int64_t* info, int cap)
         v.push_back(p.win[s].n);
         v.push_back(p.n_cells[s]);
     }
+    v.push_back(p.slots);
+    v.push_back((int64_t)p.graph_cache.size());
+    v.push_back(p.graph_replays);
     for (int i = 0; i < cap && i < (int)v.size(); ++i) info[i] = v[i];
     return (int)v.size();
 }

@@ -104,6 +104,22 @@ struct Plan {
     int64_t launches[5] = {0, 0, 0, 0, 0};
     double* dots = nullptr;               // 2P doubles: gradient dot products (addker_vjp)
     int* counters = nullptr;              // work counters of the persistent kernels (zeroed per launch)
+    // CUDA graphs of repeated products (addker_set_graphs): a product whose arguments repeat those of
+    // the previous call is captured once and replayed; any change of buffers or scalars clears them
+    struct GraphKey {
+        const float* v;
+        float *Kv, *dK;
+        int nrhs, window, mode;
+        bool operator==(const GraphKey& o) const
+        {
+            return v == o.v && Kv == o.Kv && dK == o.dK && nrhs == o.nrhs && window == o.window && mode == o.mode;
+        }
+    };
+    bool graphs = true;
+    std::vector<std::pair<GraphKey, cudaGraphExec_t>> graph_cache;   // most recent last
+    GraphKey last_key = {nullptr, nullptr, nullptr, 0, 0, -1};
+    cudaStream_t cap_stream = nullptr;
+    int64_t graph_replays = 0;
 };
 
 // Launch a kernel on st. With pdl the launch carries the programmatic-serialisation attribute (the

@@ -140,3 +140,44 @@ def test_host_entry_batched(torch_cuda):
     op.matvec_all_host(vh, Kh, dKh, nrhs)
     assert rel(Kh.reshape(nrhs, wl.N).t(), Kd.cpu()) < TOL
     assert rel(dKh.reshape(nrhs, wl.P, wl.N).permute(1, 2, 0), dKd.cpu()) < TOL
+
+
+def test_graph_replay_matches_eager(torch_cuda):
+    """Repeated identical products are captured and replayed as CUDA graphs; results match the eager
+    path, and set_params / slot growth invalidate the captured graphs."""
+    torch = torch_cuda
+    wl = workloads.make("c3", N=2500)
+    # (N, 3) view of column-major storage: the binding passes it without a copy, so the pointer repeats
+    V = torch.from_numpy(np.ascontiguousarray(wl.vector(nrhs=3).T)).cuda().t()
+    op = make_op(torch, wl)
+    op.set_graphs(False)
+    K0, D0 = op.matvec_all(V)
+    op.set_graphs(True)
+    Kv = torch.empty_like(K0.t().contiguous()).reshape(-1)
+    dK = torch.empty(wl.P * wl.N * 3, device="cuda")
+    outs = []
+    for _ in range(4):                           # eager, capture, replay, replay
+        Kv.zero_(); dK.zero_()
+        k, d = op.matvec_all(V, out_Kv=Kv, out_dK=dK)
+        outs.append((k.cpu(), d.cpu()))
+    for k, d in outs:
+        assert rel(k, K0.cpu()) < TOL and rel(d, D0.cpu()) < TOL
+    info = op.info()
+    assert info["graphs"] == 1 and info["graph_replays"] == 2 and info["slots"] == 4
+    # new hyperparameters: the replay must use them
+    op.set_params(ell=[e * 1.3 for e in wl.ell], sigma_f=1.7)
+    for _ in range(3):
+        k, d = op.matvec_all(V, out_Kv=Kv, out_dK=dK)
+    op.set_graphs(False)
+    k2, d2 = op.matvec_all(V)
+    assert rel(k.cpu(), k2.cpu()) < TOL and rel(d.cpu(), d2.cpu()) < TOL
+    # growing the slots (9 right-hand sides) discards graphs that point at the old grids
+    op.set_graphs(True)
+    V9 = torch.from_numpy(wl.vector(nrhs=9)).cuda()
+    for _ in range(3):
+        k9, _ = op.matvec_all(V9)
+    for _ in range(3):
+        k, d = op.matvec_all(V, out_Kv=Kv, out_dK=dK)
+    assert rel(k.cpu(), k2.cpu()) < TOL and rel(d.cpu(), d2.cpu()) < TOL
+    op.set_graphs(False)
+    assert rel(op.matvec(V9).cpu(), k9.cpu()) < TOL
