@@ -123,6 +123,18 @@ int addker_set_params(addker_plan* plan, const double* ell, double sigma_f);
  */
 int addker_set_graphs(addker_plan* plan, int enable);
 
+/*
+ * Autotuning of the work-item size: the spread and gather kernels take the points of each non-empty
+ * grid cell in work items of at most `chunk` points (default 256), their scheduling grain. This call
+ * times the fused product (addker_matvec_all semantics) on v (device, N x nrhs, column-major) for
+ * chunk in {64, 128, 256, 512, 1024}: one warm-up and three timed products each, without graphs. The
+ * fastest is kept for later products; chosen (host, may be NULL) receives it and times (host, may be
+ * NULL) up to `cap` per-candidate milliseconds per product, in the order above. Allocates and frees
+ * its own output buffers; synchronous on the plan's stream. The paper has no counterpart (its
+ * library runs on the CPU): this is a scheduling choice of the GPU path.
+ */
+int addker_autotune(addker_plan* plan, const float* v, int nrhs, int* chosen, double* times, int cap);
+
 /* Set the CUDA stream (cudaStream_t, NULL = legacy default) used by later products. */
 int addker_set_stream(addker_plan* plan, void* stream);
 
@@ -206,7 +218,7 @@ int addker_prescale(const float* X, int64_t N, int d, const int* win_off, const 
  *   [0] N  [1] P  [2] number of work items over all windows  [3] bytes of device memory owned
  *   then per window s: [4+4s] d_s  [5+4s] M_s  [6+4s] n_s  [7+4s] number of non-empty cells,
  *   then [4+4P] right-hand-side slots allocated  [5+4P] captured product graphs held
- *   [6+4P] product graph replays so far.
+ *   [6+4P] product graph replays so far  [7+4P] points per work item at most.
  * Returns the number of values available.
  */
 int addker_info(const addker_plan* plan, int64_t* info, int cap);

@@ -187,6 +187,18 @@ class AddKer:
         """Replay repeated identical products as CUDA graphs (default on); False launches every kernel."""
         native.check(self._ready().addker_set_graphs(self._plan, 1 if enable else 0), "addker_set_graphs")
 
+    AUTOTUNE_CHUNKS = (64, 128, 256, 512, 1024)
+
+    def autotune(self, v):
+        """Time the fused product on v ((N,) or (N, nrhs)) for each work-item size in AUTOTUNE_CHUNKS and
+        keep the fastest. Returns (chosen chunk, {chunk: ms per product})."""
+        vv, nrhs = self._rhs(v)
+        chosen = ctypes.c_int(0)
+        times = (ctypes.c_double * len(self.AUTOTUNE_CHUNKS))()
+        native.check(self._ready().addker_autotune(self._plan, ctypes.c_void_p(vv.data_ptr()), nrhs,
+                                                    ctypes.byref(chosen), times, len(times)), "addker_autotune")
+        return chosen.value, dict(zip(self.AUTOTUNE_CHUNKS, list(times)))
+
     STAGES = ("clear", "spread", "transform", "gather", "window_sum")
 
     def profile(self, enable=True):
@@ -206,7 +218,7 @@ class AddKer:
         native.check(native.lib().addker_sync(self._plan), "addker_sync")
 
     def info(self):
-        cap = 7 + 4 * self.P
+        cap = 8 + 4 * self.P
         buf = (ctypes.c_int64 * cap)()
         n = native.lib().addker_info(self._plan, buf, cap)
         vals = list(buf[:n])
@@ -214,7 +226,7 @@ class AddKer:
         return {"N": vals[0], "P": vals[1], "items": vals[2], "device_bytes": vals[3],
                 "windows": [dict(d=vals[4 + 4 * s], M=vals[5 + 4 * s], n=vals[6 + 4 * s], cells=vals[7 + 4 * s])
                             for s in range(self.P)],
-                "slots": vals[e], "graphs": vals[e + 1], "graph_replays": vals[e + 2]}
+                "slots": vals[e], "graphs": vals[e + 1], "graph_replays": vals[e + 2], "chunk": vals[e + 3]}
 
     def debug_stage(self, window, stage, v):
         """Stage 0: spread grid (n^d doubles); stage 1: adjoint NFFT S_k (complex M^d). Synchronous."""

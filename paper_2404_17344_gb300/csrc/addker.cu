@@ -71,6 +71,9 @@ void release(Plan& p)
     clear_graphs(p);
     if (p.cap_stream) cudaStreamDestroy(p.cap_stream);
     p.cap_stream = nullptr;
+    if (p.items) cudaFree(p.items);
+    p.items = nullptr;
+    p.items_cap = 0;
     for (void* a : p.allocations) cudaFree(a);
     p.allocations.clear();
     for (void* a : p.slot_allocs) cudaFree(a);
@@ -549,7 +552,7 @@ int upload_scales(Plan& p)
     return ADDKER_OK;
 }
 
-int setup_window(Plan& p, int s, const float* X, int* keys, int* flag, std::vector<int4>* lists)
+int setup_window(Plan& p, int s, const float* X, int* keys, int* flag)
 {
     WinDev& w = p.win[s];
     const int D = w.D, n = w.n;
@@ -578,29 +581,25 @@ int setup_window(Plan& p, int s, const float* X, int* keys, int* flag, std::vect
     CK(cudaMemcpy(bh, bounds, sizeof(bh), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(&fl, flag, sizeof(int), cudaMemcpyDeviceToHost));
     if (fl) { cudaFree(hist); return ADDKER_EDOMAIN; }
-    // offsets, items (chunks of at most kItemPoints points per cell, heaviest first)
+    // offsets and the non-empty cells (first point, count, packed cell, window); work items are cut
+    // from the cells by build_items
     std::vector<int> off(cells);
     int64_t acc = 0;
-    std::vector<int4> items;
-    int ncell = 0;
+    std::vector<int4>& cl = p.cells[s];
+    cl.clear();
     for (int64_t k = 0; k < cells; ++k) {
         off[k] = (int)acc;
         int cnt = h[k];
         if (cnt > 0) {
-            ++ncell;
             int c[3] = {0, 0, 0};
             int64_t rem = k;
             for (int t = D - 1; t >= 0; --t) { c[t] = (int)(rem % n); rem /= n; }
             int packed = c[0] | (c[1] << 8) | (c[2] << 16);
-            for (int st = 0; st < cnt; st += kItemPoints)
-                items.push_back(make_int4((int)acc + st, std::min(kItemPoints, cnt - st), packed, s));
+            cl.push_back(make_int4((int)acc, cnt, packed, s));
         }
         acc += cnt;
     }
-    std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) { return a.y > b.y; });
-    p.n_cells[s] = ncell;
-    std::vector<int4>& dst = lists[p.kind[s]];
-    dst.insert(dst.end(), items.begin(), items.end());
+    p.n_cells[s] = (int)cl.size();
     // scatter
     CK(cudaMemcpy(hist, off.data(), sizeof(int) * cells, cudaMemcpyHostToDevice));
     float4* pts;
@@ -702,6 +701,43 @@ struct Stage {                            // brackets one stage of a product wit
 int vec_ok(const Plan& p, const float* out, int64_t ld)
 {
     return (p.N % 4 == 0) && (ld % 4 == 0) && (reinterpret_cast<uintptr_t>(out) % 16 == 0);
+}
+
+// Work items: every non-empty cell's points in chunks of at most `chunk`, heaviest first within a
+// window; one device array holding the kernel kinds one after another (item_begin[k][s] absolute).
+// The chunk is the scheduling grain of the spread and gather kernels (addker_autotune chooses it).
+int build_items(Plan& p, int chunk)
+{
+    std::vector<int4> lists[kKinds];
+    for (int k = 0; k < kKinds; ++k) p.item_begin[k].assign(1, 0);
+    for (int s = 0; s < p.P; ++s) {
+        std::vector<int4> items;
+        for (const int4& c : p.cells[s])
+            for (int st = 0; st < c.y; st += chunk) items.push_back(make_int4(c.x + st, std::min(chunk, c.y - st), c.z, s));
+        std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) { return a.y > b.y; });
+        std::vector<int4>& dst = lists[p.kind[s]];
+        dst.insert(dst.end(), items.begin(), items.end());
+        for (int k = 0; k < kKinds; ++k) p.item_begin[k].push_back((int)lists[k].size());
+    }
+    std::vector<int4> all;
+    for (int k = 0; k < kKinds; ++k) {
+        const int base = (int)all.size();
+        for (int& b : p.item_begin[k]) b += base;
+        all.insert(all.end(), lists[k].begin(), lists[k].end());
+    }
+    if ((int64_t)all.size() > p.items_cap) {
+        if (p.items) cudaFree(p.items);
+        p.items = nullptr;
+        p.items_cap = 0;
+        if (cudaMalloc(&p.items, sizeof(int4) * all.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return ADDKER_ENOMEM;
+        }
+        p.items_cap = (int64_t)all.size();
+    }
+    if (!all.empty()) CK(cudaMemcpy(p.items, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice));
+    p.chunk = chunk;
+    return ADDKER_OK;
 }
 
 // Per-window grids for `want` right-hand sides at once (grid, h and the D = 3 transform buffers, one
@@ -1055,31 +1091,15 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
     int* keys = nullptr;
     int* flag = nullptr;
     int status = ADDKER_OK;
-    std::vector<int4> lists[kKinds];
-    for (int k = 0; k < kKinds; ++k) p.item_begin[k].assign(1, 0);
+    p.cells.assign(P, {});
     if (cudaMalloc(&keys, sizeof(int) * (size_t)(N + 1)) != cudaSuccess) status = ADDKER_ENOMEM;
     if (status == ADDKER_OK) {
         flag = keys + N;
         if (cudaMemset(flag, 0, sizeof(int)) != cudaSuccess) status = ADDKER_ECUDA;
     }
-    for (int s = 0; s < P && status == ADDKER_OK; ++s) {
-        status = setup_window(p, s, points, keys, flag, lists);
-        for (int k = 0; k < kKinds; ++k) p.item_begin[k].push_back((int)lists[k].size());
-    }
+    for (int s = 0; s < P && status == ADDKER_OK; ++s) status = setup_window(p, s, points, keys, flag);
     if (keys) cudaFree(keys);
-    if (status == ADDKER_OK) {
-        // one device array, the kinds one after another; item_begin becomes absolute
-        std::vector<int4> all;
-        for (int k = 0; k < kKinds; ++k) {
-            const int base = (int)all.size();
-            for (int& b : p.item_begin[k]) b += base;
-            all.insert(all.end(), lists[k].begin(), lists[k].end());
-        }
-        status = dalloc(p, &p.items, std::max<int64_t>(1, (int64_t)all.size()));
-        if (status == ADDKER_OK && !all.empty() &&
-            cudaMemcpy(p.items, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-            status = ADDKER_ECUDA;
-    }
+    if (status == ADDKER_OK) status = build_items(p, kItemPoints);
     if (status == ADDKER_OK) status = dalloc(p, &p.wins_dev, P);
     if (status == ADDKER_OK) status = dalloc(p, &p.scale_dev, 3 * P);
     if (status == ADDKER_OK) status = dalloc(p, &p.dots, 2 * P);
@@ -1123,6 +1143,57 @@ int addker_set_graphs(addker_plan* plan, int enable)
     clear_graphs(p);
     p.graphs = enable == 1;
     return ADDKER_OK;
+}
+
+int addker_autotune(addker_plan* plan, const float* v, int nrhs, int* chosen, double* times, int cap)
+{
+    if (!plan || !v || nrhs < 1) return ADDKER_EINVAL;
+    Plan& p = plan->p;
+    if (!valid_stream_ptrs(v)) return ADDKER_EINVAL;
+    static const int cand[] = {64, 128, 256, 512, 1024};
+    constexpr int nc = sizeof(cand) / sizeof(cand[0]);
+    CS(ensure_slots(p, nrhs));
+    float *Kv = nullptr, *dK = nullptr;
+    if (cudaMalloc(&Kv, sizeof(float) * (size_t)p.N * nrhs) != cudaSuccess ||
+        cudaMalloc(&dK, sizeof(float) * (size_t)p.N * p.P * nrhs) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(Kv);
+        return ADDKER_ENOMEM;
+    }
+    const bool graphs = p.graphs, prof = p.prof;
+    p.graphs = false;
+    p.prof = false;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    int status = ADDKER_OK, best = p.chunk;
+    double best_ms = 1e300;
+    for (int c = 0; c < nc && status == ADDKER_OK; ++c) {
+        CK(cudaStreamSynchronize(p.stream));
+        status = build_items(p, cand[c]);
+        if (status == ADDKER_OK) status = product_all(p, v, nrhs, Kv, dK, -1, 0);       // warm-up
+        cudaEventRecord(a, p.stream);
+        for (int rep = 0; rep < 3 && status == ADDKER_OK; ++rep) status = product_all(p, v, nrhs, Kv, dK, -1, 0);
+        cudaEventRecord(b, p.stream);
+        float ms = 0.f;
+        if (status == ADDKER_OK && cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) {
+            if (times && c < cap) times[c] = ms / 3.0;
+            if (ms / 3.0 < best_ms) { best_ms = ms / 3.0; best = cand[c]; }
+        } else if (status == ADDKER_OK) {
+            status = ADDKER_ECUDA;
+        }
+    }
+    cudaStreamSynchronize(p.stream);
+    if (status == ADDKER_OK) status = build_items(p, best);
+    clear_graphs(p);
+    p.graphs = graphs;
+    p.prof = prof;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(Kv);
+    cudaFree(dK);
+    if (status == ADDKER_OK && chosen) *chosen = best;
+    return status;
 }
 
 int addker_set_stream(addker_plan* plan, void* stream)
@@ -1315,6 +1386,7 @@ int addker_info(const addker_plan* plan, int64_t* info, int cap)
     v.push_back(p.slots);
     v.push_back((int64_t)p.graph_cache.size());
     v.push_back(p.graph_replays);
+    v.push_back(p.chunk);
     for (int i = 0; i < cap && i < (int)v.size(); ++i) info[i] = v[i];
     return (int)v.size();
 }

@@ -28,7 +28,7 @@ constexpr int kMaxRhsChunk = 8;         // right-hand sides processed together b
 // kernel kinds of the item lists: m = 4 fast kernels for D = 3, 1, 2, then the generic ones for D = 1, 2, 3
 enum { kKindFast3 = 0, kKindLow1 = 1, kKindLow2 = 2, kKindGen1 = 3, kKindGen2 = 4, kKindGen3 = 5, kKinds = 6 };
 inline int kind_of(int D, int m) { return m == 4 ? (D == 3 ? kKindFast3 : D) : 2 + D; }
-constexpr int kItemPoints = 256;        // points per work item (one warp)
+constexpr int kItemPoints = 256;        // default points per work item (one warp); see build_items
 constexpr int kMaxBandwidth = 64;
 
 // Piecewise polynomial form of the window used by every spreading/interpolation kernel: for a
@@ -83,6 +83,9 @@ struct Plan {
     // work items of all windows in one device array, grouped by kernel kind and, within a kind, by
     // window: items of window s are [item_begin[k][s], item_begin[k][s+1]) for its kind k = kind[s]
     int4* items = nullptr;
+    int64_t items_cap = 0;
+    int chunk = kItemPoints;              // points per work item at most
+    std::vector<std::vector<int4>> cells; // per window: non-empty cells (first point, count, packed cell, s)
     std::vector<int> item_begin[kKinds];
     std::vector<int> kind;
     int slots = 0;                        // right-hand-side slots allocated per window

@@ -41,6 +41,7 @@ SIGNATURES = {
     "addker_set_params": (_I, [_VP, _VP, _D]),
     "addker_set_stream": (_I, [_VP, _VP]),
     "addker_set_graphs": (_I, [_VP, _I]),
+    "addker_autotune": (_I, [_VP, _VP, _I, _VP, _VP, _I]),
     "addker_matvec": (_I, [_VP, _VP, _VP, _I]),
     "addker_dmatvec": (_I, [_VP, _I, _VP, _VP, _I]),
     "addker_matvec_all": (_I, [_VP, _VP, _VP, _VP, _I]),

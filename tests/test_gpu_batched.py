@@ -181,3 +181,20 @@ def test_graph_replay_matches_eager(torch_cuda):
     assert rel(k.cpu(), k2.cpu()) < TOL and rel(d.cpu(), d2.cpu()) < TOL
     op.set_graphs(False)
     assert rel(op.matvec(V9).cpu(), k9.cpu()) < TOL
+
+
+@pytest.mark.parametrize("cfg,N,nrhs", [("c3", 3000, 1), ("c1", 5000, 3)])
+def test_autotune_keeps_results(torch_cuda, cfg, N, nrhs):
+    """The autotuner re-cuts the work items for every candidate size; the product afterwards (and its
+    graph replays) matches the product before, and the chosen size is one of the candidates."""
+    torch = torch_cuda
+    wl = workloads.make(cfg, N=N)
+    V = torch.from_numpy(wl.vector(nrhs=nrhs) if nrhs > 1 else wl.vector()).cuda()
+    op = make_op(torch, wl)
+    K0, D0 = op.matvec_all(V)
+    chosen, times = op.autotune(V)
+    assert chosen in op.AUTOTUNE_CHUNKS and op.info()["chunk"] == chosen
+    assert all(t > 0 for t in times.values())
+    for _ in range(3):
+        K1, D1 = op.matvec_all(V)
+    assert rel(K1.cpu(), K0.cpu()) < TOL and rel(D1.cpu(), D0.cpu()) < TOL
