@@ -23,5 +23,5 @@ invariants), except the absolute error level of the regularised periodisation
 against the paper's figures, which are not available ("parity unpinned" for that
 one number only; the regularisation itself is pinned by its defining conditions).
 """
-from . import bounds, fastsum, gradients, kernels, window  # noqa: F401
+from . import bounds, fastsum, gp, gradients, kernels, window  # noqa: F401
 from ._clib import build  # noqa: F401
