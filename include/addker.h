@@ -135,6 +135,41 @@ int addker_set_graphs(addker_plan* plan, int enable);
  */
 int addker_autotune(addker_plan* plan, const float* v, int nrhs, int* chosen, double* times, int cap);
 
+/*
+ * Conjugate gradients for the regression system (K + beta I) x = y (Sec. 3.3, eq. "regression_system";
+ * the paper solves it with unpreconditioned CG to a relative residual tolerance), for nrhs independent
+ * columns at once.
+ *   beta    regularisation (>= 0; K + beta I must be positive definite)
+ *   y       device, N x nrhs float32, column-major (column j at y + j N)
+ *   x       device, N x nrhs float32: the initial guess in, the solution out
+ *   tol     stop a column once ||y - (K + beta I) x|| <= tol ||y|| (> 0); the residual is the CG
+ *           recurrence's, FP64 norms of FP32 vectors
+ *   maxit   iterations at most (>= 0); a column still above tol after maxit keeps its last iterate
+ *   iters, relres  host, nrhs each (may be NULL): iterations taken and the final relative residual
+ * Each iteration is one batched product (graph-replayed after the first) plus three vector kernels with
+ * FP64 dot products; the host reads the nrhs residual norms once per iteration. A column with y = 0
+ * returns x = 0. Synchronous. EINVAL for bad sizes or non-device pointers, ENOMEM for workspace.
+ */
+int addker_cg(addker_plan* plan, double beta, const float* y, float* x, int nrhs, double tol, int maxit,
+              int* iters, double* relres);
+
+/*
+ * Gradient of the GP log marginal likelihood L = -1/2 y^T A^{-1} y - 1/2 log det A - N/2 log 2 pi,
+ * A = K + beta I, with respect to (ell_1 .. ell_P, sigma_f, beta):
+ *   dL/dtheta = 1/2 alpha^T (dA/dtheta) alpha - 1/2 tr(A^{-1} dA/dtheta),   alpha = A^{-1} y,
+ * the trace by Hutchinson's estimator (1/m) sum_i (A^{-1} z_i)^T (dA/dtheta) z_i over the m probes
+ * given in Z (the caller draws them, e.g. Rademacher). dA/d ell_s are the derivative-kernel products
+ * (Sec. 3.3), dA/d sigma_f = (2/sigma_f) K, dA/d beta = I. One CG solve (addker_cg semantics, x0 = 0)
+ * with the 1 + m columns [y, Z], then one fused product on [alpha, Z], then FP64 dot products.
+ *   y      device, N float32;  Z  device, N x m float32 column-major (NULL if m = 0: no trace term)
+ *   grad   host, P + 2 doubles out;  fit  host, 1 double out (y^T alpha; may be NULL)
+ *   alpha  device, N float32 out (may be NULL);  iters  host, 1 int out: the most CG iterations of
+ *          any column (may be NULL)
+ * Synchronous. EINVAL / ENOMEM as addker_cg.
+ */
+int addker_gp_grad(addker_plan* plan, double beta, const float* y, const float* Z, int m, double tol, int maxit,
+                   double* grad, double* fit, float* alpha, int* iters);
+
 /* Set the CUDA stream (cudaStream_t, NULL = legacy default) used by later products. */
 int addker_set_stream(addker_plan* plan, void* stream);
 

@@ -187,6 +187,43 @@ class AddKer:
         """Replay repeated identical products as CUDA graphs (default on); False launches every kernel."""
         native.check(self._ready().addker_set_graphs(self._plan, 1 if enable else 0), "addker_set_graphs")
 
+    def cg(self, y, beta, tol=1e-3, maxit=1000, x0=None):
+        """Solve (K + beta I) x = y by conjugate gradients (addker_cg). y is (N,) or (N, nrhs); returns
+        (x shaped like y, iterations per column, relative residual per column)."""
+        torch = _torch()
+        yy, nrhs = self._rhs(y)
+        x = torch.zeros_like(yy) if x0 is None else self._rhs(x0)[0].clone()
+        iters = (ctypes.c_int * nrhs)()
+        rel = (ctypes.c_double * nrhs)()
+        native.check(self._ready().addker_cg(self._plan, float(beta), ctypes.c_void_p(yy.data_ptr()),
+                                              ctypes.c_void_p(x.data_ptr()), nrhs, float(tol), int(maxit), iters, rel),
+                     "addker_cg")
+        return self._shape_out(x.reshape(-1), nrhs, (self.N,)), list(iters), list(rel)
+
+    def gp_grad(self, y, beta, Z=None, tol=1e-3, maxit=1000):
+        """Gradient of the GP log marginal likelihood in (ell_1..ell_P, sigma_f, beta) with Hutchinson
+        probes Z ((N, m), or None for no trace term) (addker_gp_grad). Returns (grad [P+2] float64 numpy,
+        y^T alpha, alpha [N], CG iterations)."""
+        import numpy as np
+        torch = _torch()
+        yv = _dev_f32(y, "y")
+        if yv.shape != (self.N,):
+            raise ValueError("y must be (N,)")
+        m = 0
+        zp = None
+        if Z is not None:
+            zz, m = self._rhs(Z)
+            zp = ctypes.c_void_p(zz.data_ptr())
+        grad = (ctypes.c_double * (self.P + 2))()
+        fit = ctypes.c_double(0.0)
+        alpha = torch.empty(self.N, device=yv.device, dtype=torch.float32)
+        iters = ctypes.c_int(0)
+        native.check(self._ready().addker_gp_grad(self._plan, float(beta), ctypes.c_void_p(yv.data_ptr()), zp, m,
+                                                   float(tol), int(maxit), grad, ctypes.byref(fit),
+                                                   ctypes.c_void_p(alpha.data_ptr()), ctypes.byref(iters)),
+                     "addker_gp_grad")
+        return np.array(list(grad)), fit.value, alpha, iters.value
+
     AUTOTUNE_CHUNKS = (64, 128, 256, 512, 1024)
 
     def autotune(self, v):

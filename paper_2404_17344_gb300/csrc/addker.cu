@@ -875,10 +875,12 @@ int product_chunks(Plan& p, const float* v, int nrhs, float* Kv, float* dK, int 
     return ADDKER_OK;
 }
 
+}  // namespace
+
 // All products go through here. With graphs on (and no stage profiling, and a stream that is not itself
 // being captured), the second consecutive call with the same arguments is captured on a private stream
 // and every later one replays the graph on the plan's stream: one launch instead of one per kernel.
-int product_all(Plan& p, const float* v, int nrhs, float* Kv, float* dK, int window, int mode)
+int addker::product_all(Plan& p, const float* v, int nrhs, float* Kv, float* dK, int window, int mode)
 {
     // a batch that cannot get more slots runs in single-right-hand-side chunks
     if (ensure_slots(p, nrhs) != ADDKER_OK) CS(ensure_slots(p, 1));
@@ -927,6 +929,8 @@ int product_all(Plan& p, const float* v, int nrhs, float* Kv, float* dK, int win
     CK(cudaGraphLaunch(exec, p.stream));
     return ADDKER_OK;
 }
+
+namespace {
 
 }  // namespace
 
@@ -1194,6 +1198,24 @@ int addker_autotune(addker_plan* plan, const float* v, int nrhs, int* chosen, do
     cudaFree(dK);
     if (status == ADDKER_OK && chosen) *chosen = best;
     return status;
+}
+
+int addker_cg(addker_plan* plan, double beta, const float* y, float* x, int nrhs, double tol, int maxit, int* iters,
+              double* relres)
+{
+    if (!plan || !y || !x || nrhs < 1 || !(beta >= 0.0) || !(tol > 0.0) || maxit < 0) return ADDKER_EINVAL;
+    if (!valid_stream_ptrs(y) || !valid_stream_ptrs(x)) return ADDKER_EINVAL;
+    return cg_solve(plan->p, beta, y, x, nrhs, tol, maxit, iters, relres);
+}
+
+int addker_gp_grad(addker_plan* plan, double beta, const float* y, const float* Z, int m, double tol, int maxit,
+                   double* grad, double* fit, float* alpha, int* iters)
+{
+    if (!plan || !y || !grad || m < 0 || (m > 0 && !Z) || !(beta >= 0.0) || !(tol > 0.0) || maxit < 0)
+        return ADDKER_EINVAL;
+    if (!valid_stream_ptrs(y) || (m > 0 && !valid_stream_ptrs(Z)) || (alpha && !valid_stream_ptrs(alpha)))
+        return ADDKER_EINVAL;
+    return gp_grad(plan->p, beta, y, Z, m, tol, maxit, grad, fit, alpha, iters);
 }
 
 int addker_set_stream(addker_plan* plan, void* stream)

@@ -263,6 +263,15 @@ cudaError_t launch_gather(const Plan& p, int window_or_all, float* outK, int64_t
 cudaError_t launch_gather_grad(const Plan& p, int pass, const float* other, float* ks, float* grad_x,
                                cudaStream_t st, int* count);
 
+// Products of a plan (addker.cu): nrhs columns v + j N, mode 0 fused (Kv and/or dK), 1 one window's
+// derivative, 2 the shared-length-scale derivative; chunked, graph-replayed when repeated.
+int product_all(Plan& p, const float* v, int nrhs, float* Kv, float* dK, int window, int mode);
+// Regression system and GP training (solver.cu).
+int cg_solve(Plan& p, double beta, const float* Y, float* X, int nrhs, double tol, int maxit, int* iters,
+             double* relres);
+int gp_grad(Plan& p, double beta, const float* y, const float* Z, int m, double tol, int maxit, double* grad,
+            double* fit, float* alpha_out, int* iters);
+
 // Building blocks used without a plan (addker_fastsum_noalloc).
 void window_poly_for(int m, double sigma_os, WinPoly* poly);
 int multipliers_with_scratch(const WinDev& w, double ell, int p_opt, double eps_B, const WinPoly& poly,
