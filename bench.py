@@ -5,6 +5,8 @@ of 3 consecutive features, ell = (0.3, 0.5, 1.0), sigma_f = 1, bandwidth M = 32,
 cutoff m = 4 (N(0,1) features scaled into the ball of radius 1/4 - eps_B/2; synthetic, seeded).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--N 1000000]
+  python bench.py --mode batched [--nrhs 64]        (secondary: 7 mixed windows, 64 right-hand sides)
+  python bench.py --mode gp [--nrhs 8 --beta 1 --tol 1e-3]   (secondary: GP gradient, N = 2e6)
 
 --gpus N > 1 runs under torchrun, one rank per GPU: independent replicas (the product needs no
 exchange between GPUs at this size), weak scaling; value = all ranks' units / max-over-ranks time.
@@ -319,6 +321,118 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def _setup_secondary(args, local_rank):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local_rank)
+    return torch, dev, gpu_id
+
+
+def run_batched(args, rank, world, local_rank):
+    """Secondary workload (multi-RHS batching): the mixed-window configuration (N = 1e6, d = 15, windows of
+    3,3,3,2,2,1,1, M = 32 for 3-D and 16 for 1-D/2-D windows) with 64 right-hand sides per step; one unit
+    = K v + all dK/d ell_s v for one right-hand side. The work-item size is autotuned first."""
+    import numpy as np
+    torch, dev, gpu_id = _setup_secondary(args, local_rank)
+    import workloads
+    from paper_2404_17344_gb300 import AddKer
+    N = args.N if args.N != 1_000_000 else 1_000_000
+    R = args.nrhs
+    wl = workloads.make("c3", N=N)
+    op = AddKer(torch.from_numpy(wl.points).to(dev), wl.windows, wl.ell, wl.sigma_f, wl.bandwidth, wl.cutoff)
+    Vnp = wl.vector(nrhs=R)
+    V = torch.from_numpy(np.ascontiguousarray(Vnp.T)).to(dev).t()          # column-major (N, R) view
+    chunk, tune_ms = op.autotune(V[:, :8])
+    Kv = torch.empty(N * R, device=dev)
+    dK = torch.empty(N * wl.P * R, device=dev)
+    for _ in range(args.warmup):
+        op.matvec_all(V, out_Kv=Kv, out_dK=dK)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(gpu_id) as clk:
+        for a, b in ev:
+            a.record()
+            op.matvec_all(V, out_Kv=Kv, out_dK=dK)
+            b.record()
+        torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    # accuracy: right-hand sides 0 and R-1 on 256 sampled rows against the FP64 CPU NFFT
+    import oracle
+    rows = np.random.default_rng(0).choice(N, 256, replace=False)
+    acc = {}
+    Kh = Kv.reshape(R, N).cpu().numpy()
+    for j in (0, R - 1):
+        Kn, _ = oracle.fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f, Vnp[:, j].astype(np.float64),
+                                          wl.bandwidth, wl.cutoff, rows=rows)
+        acc[f"Kv_rhs{j}_vs_fp64_nfft"] = float(np.linalg.norm(Kh[j][rows] - Kn) / np.linalg.norm(Kn))
+    out = {"metric": "batched additive K·V + dK/d(ell)·V, right-hand-side units per sec, N=1M, 7 mixed windows",
+           "value": R / (ms / 1e3), "unit": "units/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": f"c3-shaped at N={N}: d=15, windows 3,3,3,2,2,1,1, ell log-U[0.1,2], M=32/16, "
+                                  f"m=4, U[-1,1] features scaled into the ball, {R} right-hand sides per step",
+                      "N": N, "nrhs": R, "chunk": chunk, "autotune_ms": tune_ms},
+           "clocks": clk.summary(), "accuracy": acc, "plan": {k: v for k, v in op.info().items() if k != "windows"}}
+    print(json.dumps(out), flush=True)
+    op.close()
+
+
+def run_gp(args, rank, world, local_rank):
+    """Secondary workload (GP training): the correlated-Gaussian configuration (N = 2e6, d = 24, eight
+    windows of 3, ell = 0.5, M = 32) with regression targets from random Fourier features plus noise;
+    one step = one gradient of the GP log marginal likelihood in (ell_1..ell_8, sigma_f, beta): CG on
+    (K + beta I) with 1 + m right-hand sides [y, z_1..z_m] (Rademacher probes, Hutchinson) to the relative
+    residual tolerance the paper's KRR uses (or at most --maxit iterations: unpreconditioned CG on
+    K + beta I at N = 2e6 needs thousands, so the default caps it and reports the residual reached), then
+    one fused product on [alpha, z_1..z_m]."""
+    import numpy as np
+    torch, dev, gpu_id = _setup_secondary(args, local_rank)
+    import workloads
+    from paper_2404_17344_gb300 import AddKer
+    N = args.N if args.N != 1_000_000 else 2_000_000
+    m = args.nrhs - 1
+    wl = workloads.make("c4", N=N)
+    op = AddKer(torch.from_numpy(wl.points).to(dev), wl.windows, wl.ell, wl.sigma_f, wl.bandwidth, wl.cutoff)
+    y = torch.from_numpy(wl.targets()).to(dev)
+    Z = torch.from_numpy(wl.probes(m)).to(dev)
+    beta, tol = args.beta, args.tol
+    for _ in range(max(1, args.warmup // 3)):
+        g, fit, alpha, iters = op.gp_grad(y, beta, Z, tol=tol, maxit=args.maxit)
+    torch.cuda.synchronize()
+    ts, its = [], []
+    with ClockSampler(gpu_id) as clk:
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g, fit, alpha, iters = op.gp_grad(y, beta, Z, tol=tol, maxit=args.maxit)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+            its.append(iters)
+    ms = statistics.mean(ts)
+    # relative residual of alpha, by one more product
+    Ka = op.matvec(alpha)
+    relres = float(torch.linalg.norm(y - Ka - beta * alpha) / torch.linalg.norm(y))
+    out = {"metric": "GP log-marginal-likelihood gradients per sec (Hutchinson, CG), N=2M, 8 windows of 3",
+           "value": 1e3 / ms, "unit": "gradients/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": f"c4-shaped at N={N}: d=24, correlated Gaussian features, 8 windows of 3, ell=0.5, "
+                                  "M=32, m=4; y = random Fourier features + 0.1 noise",
+                      "N": N, "probes": m, "beta": beta, "cg_tol": tol, "cg_maxit": args.maxit, "cg_iters": its,
+                      "alpha_relres": relres,
+                      "ms_per_cg_iteration": ms / max(1, statistics.mean(its))},
+           "grad": list(map(float, g)), "fit": fit, "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+    op.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,6 +444,13 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=100_000)
     ap.add_argument("--check-rows", type=int, default=256)
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--mode", default="product", choices=["product", "batched", "gp"],
+                    help="product: the headline fused product; batched: 7 mixed windows x 64 right-hand sides; "
+                         "gp: one GP gradient (CG + Hutchinson) per step")
+    ap.add_argument("--nrhs", type=int, default=64, help="right-hand sides per step (batched), 1 + probes (gp)")
+    ap.add_argument("--beta", type=float, default=1.0, help="gp: regularisation beta")
+    ap.add_argument("--tol", type=float, default=1e-3, help="gp: CG relative residual tolerance")
+    ap.add_argument("--maxit", type=int, default=100, help="gp: CG iterations at most")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -338,6 +459,12 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.mode == "batched":
+        run_batched(args, rank, world, local_rank)
+    elif args.mode == "gp":
+        if args.nrhs == 64:
+            args.nrhs = 8
+        run_gp(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

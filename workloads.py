@@ -20,7 +20,8 @@ Points are then multiplied by one global factor so that every point restricted
 to every window lies in the ball of radius rho = 1/4 - eps_B/2 (eps_B = 1/16);
 then all pairwise differences inside a window have norm <= 1/2 - eps_B. Length
 scales are given in these scaled units. Seeds: numpy PCG64 with
-seed = 1000 + config index for the points, +1 for v, +2 for w.
+seed = 1000 + config index for the points, +1 for v, +2 for w, +3 for regression
+targets (random Fourier features plus noise), +4 for Hutchinson probes.
 """
 from __future__ import annotations
 
@@ -61,6 +62,27 @@ class Workload:
         if nrhs == 1:
             return rng.standard_normal(self.N).astype(np.float32)
         return rng.standard_normal((nrhs, self.N)).astype(np.float32).T.copy()
+
+    def targets(self, features: int = 64, noise: float = 0.1) -> np.ndarray:
+        """Regression targets for the GP/KRR loop: a random-Fourier-feature function of the points,
+        y = sqrt(2/F) sum_f a_f cos(omega_f . x + b_f) + noise * eps, with omega_f ~ N(0, 1/ell0^2) in
+        every window's coordinates (ell0 = the median length scale), a_f, eps ~ N(0, 1),
+        b_f ~ U[0, 2 pi). Seed + 3. Shape (N,), float32."""
+        rng = np.random.Generator(np.random.PCG64(self.seed + 3))
+        feats = sorted({f for w in self.windows for f in w})
+        ell0 = float(np.median(self.ell))
+        X = self.points[:, feats].astype(np.float64)
+        omega = rng.standard_normal((features, len(feats))) / ell0
+        a = rng.standard_normal(features)
+        b = rng.uniform(0.0, 2.0 * np.pi, size=features)
+        y = np.sqrt(2.0 / features) * (np.cos(X @ omega.T + b) @ a)
+        y += noise * rng.standard_normal(self.N)
+        return y.astype(np.float32)
+
+    def probes(self, m: int) -> np.ndarray:
+        """m Rademacher probe vectors for Hutchinson's trace estimator, (N, m) float32. Seed + 4."""
+        rng = np.random.Generator(np.random.PCG64(self.seed + 4))
+        return rng.choice(np.array([-1.0, 1.0], dtype=np.float32), size=(m, self.N)).T.copy()
 
 
 def scale_into_ball(X: np.ndarray, windows, rho: float = RHO) -> np.ndarray:
