@@ -16,6 +16,9 @@ Derivatives" that it follows):
   kernels.*             kernels, regularisation, discrete Fourier coefficients
   window.*              Kaiser-Bessel window and its Fourier transform
   bounds.*              the error bounds of Sec. 3.4 and the analytic coefficients
+  gp.*                  regression system (CG), GP log marginal likelihood and its gradient,
+                        Hutchinson's trace estimator (Sec. 3.3)
+  gsi.*                 global sensitivity indices (Sec. 4, Algorithm "Computation of GSI")
 
 Parity status: every function is pinned by a CPU test against something other
 than itself (closed forms, brute force, the paper's printed constants, bounds,
@@ -23,5 +26,5 @@ invariants), except the absolute error level of the regularised periodisation
 against the paper's figures, which are not available ("parity unpinned" for that
 one number only; the regularisation itself is pinned by its defining conditions).
 """
-from . import bounds, fastsum, gp, gradients, kernels, window  # noqa: F401
+from . import bounds, fastsum, gp, gradients, gsi, kernels, window  # noqa: F401
 from ._clib import build  # noqa: F401
