@@ -170,6 +170,21 @@ int addker_cg(addker_plan* plan, double beta, const float* y, float* x, int nrhs
 int addker_gp_grad(addker_plan* plan, double beta, const float* y, const float* Z, int m, double tol, int maxit,
                    double* grad, double* fit, float* alpha, int* iters);
 
+/*
+ * Global sensitivity indices (Sec. 4, Algorithm "Computation of GSI") of the plan's fast-summation
+ * polynomial h~(x) = sum_s sum_k c_hat_k S(k, W_s) e^{2 pi i k.x^W_s} for coefficients v (device, N
+ * float32): S(k, W_s) is the adjoint NFFT of v over window s (the plan's own spread and forward
+ * transform), and the variance |c_hat_k S(k, W_s)|^2 of each frequency goes to the feature subset on
+ * which k is non-zero; subsets shared by several windows add up. Windows of any length (<= 3) and
+ * length scale use their own coefficients (the paper's algorithm assumes equal windows; the general
+ * case is the one it calls analogous). S uses the exponent sign of eq. "approx fast sum".
+ * Outputs, sorted by decreasing index: feats (host, cap x 3 ints: the subset's feature indices,
+ * ascending, padded with -1), rho (host, cap doubles: theta_u / total), total (host, may be NULL:
+ * the total variance). Returns the number of distinct non-empty subsets (>= 0; only the first cap are
+ * written) or a negative status. Synchronous.
+ */
+int addker_gsi(addker_plan* plan, const float* v, int cap, int* feats, double* rho, double* total);
+
 /* Set the CUDA stream (cudaStream_t, NULL = legacy default) used by later products. */
 int addker_set_stream(addker_plan* plan, void* stream);
 

@@ -224,6 +224,25 @@ class AddKer:
                      "addker_gp_grad")
         return np.array(list(grad)), fit.value, alpha, iters.value
 
+    def gsi(self, v):
+        """Global sensitivity indices of the fast-summation polynomial for coefficients v (addker_gsi).
+        Returns ({feature subset (tuple): rho}, total variance), subsets by decreasing rho."""
+        vv = _dev_f32(v, "v")
+        if vv.shape != (self.N,):
+            raise ValueError("v must be (N,)")
+        L = self._ready()
+        cap = sum(2 ** len(w) - 1 for w in self.windows)
+        feats = (ctypes.c_int * (3 * cap))()
+        rho = (ctypes.c_double * cap)()
+        total = ctypes.c_double(0.0)
+        n = L.addker_gsi(self._plan, ctypes.c_void_p(vv.data_ptr()), cap, feats, rho, ctypes.byref(total))
+        if n < 0:
+            native.check(n, "addker_gsi")
+        out = {}
+        for i in range(min(n, cap)):
+            out[tuple(f for f in feats[3 * i:3 * i + 3] if f >= 0)] = rho[i]
+        return out, total.value
+
     AUTOTUNE_CHUNKS = (64, 128, 256, 512, 1024)
 
     def autotune(self, v):

@@ -207,7 +207,7 @@ __global__ void k_coef_dft(const double* __restrict__ in, double* __restrict__ o
 template <int D>
 __global__ void k_multipliers(const double* __restrict__ cK, const double* __restrict__ cD, int M, int n,
                               const double* __restrict__ phat, float* __restrict__ bK, float* __restrict__ bD,
-                              float* __restrict__ dconv)
+                              float* __restrict__ dconv, float* __restrict__ chat)
 {
     int64_t total = 1;
     for (int t = 0; t < D; ++t) total *= M;
@@ -224,6 +224,7 @@ __global__ void k_multipliers(const double* __restrict__ cK, const double* __res
     bK[idx] = (float)(cK[idx] / (den * den));
     bD[idx] = (float)(cD[idx] / (den * den));
     dconv[idx] = (float)(1.0 / den);
+    if (chat) chat[idx] = (float)cK[idx];
 }
 
 // forward twiddles tf[i][kk] = e^{-2 pi i k l / n}, inverse ti[kk][i] = e^{+2 pi i k l / n},
@@ -530,9 +531,10 @@ int compute_multipliers(Plan& p, int s)
             std::swap(src[q], dst[q]);
         }
     }
-    if (w.D == 1) k_multipliers<1><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, (float*)w.bK, (float*)w.bD, (float*)w.dconv);
-    else if (w.D == 2) k_multipliers<2><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, (float*)w.bK, (float*)w.bD, (float*)w.dconv);
-    else k_multipliers<3><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, (float*)w.bK, (float*)w.bD, (float*)w.dconv);
+    float* mk[4] = {(float*)w.bK, (float*)w.bD, (float*)w.dconv, (float*)w.chat};
+    if (w.D == 1) k_multipliers<1><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, mk[0], mk[1], mk[2], mk[3]);
+    else if (w.D == 2) k_multipliers<2><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, mk[0], mk[1], mk[2], mk[3]);
+    else k_multipliers<3><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, mk[0], mk[1], mk[2], mk[3]);
     cudaError_t e = cudaGetLastError();
     cudaError_t e2 = cudaStreamSynchronize(st);
     cudaFree(a);
@@ -635,11 +637,12 @@ int setup_window(Plan& p, int s, const float* X, int* keys, int* flag)
     w.h = nullptr;
     w.buf1 = w.buf2 = nullptr;
     CS(dalloc(p, &spec, md));
-    CS(dalloc(p, &mult, 3 * md));
+    CS(dalloc(p, &mult, 4 * md));
     w.spec = spec;
     w.bK = mult;
     w.bD = mult + md;
     w.dconv = mult + 2 * md;
+    w.chat = mult + 3 * md;
     for (int t = 0; t < 3; ++t) { w.twf[t] = nullptr; w.twi[t] = nullptr; }
     for (int t = 0; t < D; ++t) {
         float2* tw;
@@ -979,9 +982,9 @@ int multipliers_with_scratch(const WinDev& w, double ell, int p_opt, double eps_
     float* bK = const_cast<float*>(w.bK);
     float* bD = const_cast<float*>(w.bD);
     float* dc = const_cast<float*>(w.dconv);
-    if (w.D == 1) k_multipliers<1><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, bK, bD, dc);
-    else if (w.D == 2) k_multipliers<2><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, bK, bD, dc);
-    else k_multipliers<3><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, bK, bD, dc);
+    if (w.D == 1) k_multipliers<1><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, bK, bD, dc, nullptr);
+    else if (w.D == 2) k_multipliers<2><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, bK, bD, dc, nullptr);
+    else k_multipliers<3><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, bK, bD, dc, nullptr);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
     return ADDKER_OK;
@@ -1216,6 +1219,15 @@ int addker_gp_grad(addker_plan* plan, double beta, const float* y, const float* 
     if (!valid_stream_ptrs(y) || (m > 0 && !valid_stream_ptrs(Z)) || (alpha && !valid_stream_ptrs(alpha)))
         return ADDKER_EINVAL;
     return gp_grad(plan->p, beta, y, Z, m, tol, maxit, grad, fit, alpha, iters);
+}
+
+int addker_gsi(addker_plan* plan, const float* v, int cap, int* feats, double* rho, double* total)
+{
+    if (!plan || !v || cap < 0 || (cap > 0 && (!feats || !rho))) return ADDKER_EINVAL;
+    if (!valid_stream_ptrs(v)) return ADDKER_EINVAL;
+    Plan& p = plan->p;
+    CS(ensure_slots(p, 1));
+    return gsi_run(p, v, cap, feats, rho, total);
 }
 
 int addker_set_stream(addker_plan* plan, void* stream)

@@ -57,6 +57,7 @@ struct WinDev {                          // copied by value into kernel paramete
     const float* bK;
     const float* bD;
     const float* dconv;                  // 1 / (n^D prod_t phi_hat(k_t)): the adjoint NFFT's deconvolution
+    const float* chat;                   // c_hat_k, the kernel's Fourier coefficients (FP32 copy; GSI)
     // per right-hand-side slots: slot r of grid and h starts at + r*gsz, of buf1 at + r*b1sz, of
     // buf2 at + r*b2sz (elements of the respective type)
     int64_t gsz, b1sz, b2sz;
@@ -271,6 +272,9 @@ int cg_solve(Plan& p, double beta, const float* Y, float* X, int nrhs, double to
              double* relres);
 int gp_grad(Plan& p, double beta, const float* y, const float* Z, int m, double tol, int maxit, double* grad,
             double* fit, float* alpha_out, int* iters);
+
+// Global sensitivity indices (gsi.cu): returns the number of feature subsets (or a negative status).
+int gsi_run(Plan& p, const float* v, int cap, int* feats, double* rho, double* total);
 
 // Building blocks used without a plan (addker_fastsum_noalloc).
 void window_poly_for(int m, double sigma_os, WinPoly* poly);
