@@ -157,13 +157,39 @@ def nfft_fastsum(x: np.ndarray, v: np.ndarray, chats, n: int, m: int, sigma: flo
     return nfft_forward(x if targets is None else targets, [c * S for c in chats], n, m, sigma)
 
 
-def window_coefficients(ell: float, d: int, M: int, p: int, eps_B: float):
-    return (kernels.coefficients(ell, d, M, p, eps_B, "gauss"),
-            kernels.coefficients(ell, d, M, p, eps_B, "der"))
+KINDS = {"gauss": ("gauss", "der", 2.0), "matern": ("matern", "matern_der", 1.0)}
+
+
+def window_coefficients(ell: float, d: int, M: int, p: int, eps_B: float, kernel: str = "gauss"):
+    kk, kd, _ = KINDS[kernel]
+    return (kernels.coefficients(ell, d, M, p, eps_B, kk),
+            kernels.coefficients(ell, d, M, p, eps_B, kd))
+
+
+def direct_matern(points, windows, ell, sigma_f: float, v, rows=None, block: int = 256):
+    """Direct FP64 sums of the additive Matern(1/2) kernel (Sec. 5): (K v)_i = sigma_f^2 sum_s sum_j
+    exp(-r_s/ell_s) v_j and (dK/d ell_s v)_i = sigma_f^2 sum_j (r_s/ell_s^2) exp(-r_s/ell_s) v_j,
+    r_s = ||x_i^W_s - x_j^W_s||; numpy, row blocks."""
+    X = np.asarray(points, dtype=np.float32).astype(np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    rows = np.arange(X.shape[0]) if rows is None else np.asarray(rows)
+    P = len(windows)
+    Kv = np.zeros(len(rows))
+    dK = np.zeros((P, len(rows)))
+    for b0 in range(0, len(rows), block):
+        rb = rows[b0:b0 + block]
+        for s, w in enumerate(windows):
+            Y = X[:, list(w)]
+            r = np.sqrt(np.sum((Y[rb][:, None, :] - Y[None, :, :]) ** 2, axis=2))
+            E = np.exp(-r / ell[s])
+            Kv[b0:b0 + block] += sigma_f ** 2 * (E @ v)
+            dK[s, b0:b0 + block] = sigma_f ** 2 * ((r / ell[s] ** 2 * E) @ v)
+    return Kv, dK
 
 
 def matvec_all(points, windows, ell, sigma_f: float, v, bandwidth, cutoff: int, p=None,
-               eps_B: float = 1.0 / 16.0, sigma: float = 2.0, level: str = "nfft", rows=None):
+               eps_B: float = 1.0 / 16.0, sigma: float = 2.0, level: str = "nfft", rows=None,
+               kernel: str = "gauss"):
     """Fused product: returns (K v, dK/d ell [P, .]) at level 'nfft' (CPU NFFT fast sum)
     or 'ndft' (exact trigonometric sum). v is one right-hand side of length N. With `rows`, the
     outputs are evaluated only at those points (all N points are still sources)."""
@@ -180,7 +206,7 @@ def matvec_all(points, windows, ell, sigma_f: float, v, bandwidth, cutoff: int, 
         d = len(w)
         M = int(bandwidth[s])
         ps = kernels.default_p(M, eps_B) if p is None else int(p)
-        cg, cd = window_coefficients(float(ell[s]), d, M, ps, eps_B)
+        cg, cd = window_coefficients(float(ell[s]), d, M, ps, eps_B, kernel)
         xs = np.ascontiguousarray(X[:, list(w)])
         xt = None if rows is None else np.ascontiguousarray(T[:, list(w)])
         if level == "nfft":
@@ -192,5 +218,5 @@ def matvec_all(points, windows, ell, sigma_f: float, v, bandwidth, cutoff: int, 
         else:
             raise ValueError(level)
         Kv += sigma_f ** 2 * outK
-        dK[s] = sigma_f ** 2 * (2.0 / ell[s]) * outD
+        dK[s] = sigma_f ** 2 * (KINDS[kernel][2] / ell[s]) * outD
     return Kv, dK

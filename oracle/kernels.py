@@ -9,6 +9,12 @@ Kernels (Sec. 3.3, eqs. "implement_gaussian_kernel" and
 
 so that K v = sigma_f^2 sum_s K_s^gauss v and dK/d ell_s v = sigma_f^2 (2/ell_s) K_s^der v.
 
+Matern(1/2) (Sec. 5, "Extension to Other Kernels"): kappa_M(r) = exp(-r/ell) and the derivative
+kernel kappa_derM(r) = (r/ell) exp(-r/ell), so that dK/d ell_s v = sigma_f^2 (1/ell_s) K_s^derM v
+(kinds 'matern' and 'matern_der'). The same boundary regularisation is applied; the kink of
+exp(-r/ell) at r = 0 stays (no near-field correction, which the paper does not describe), so its
+coefficients decay slowly and the Fourier approximation is far less accurate than the Gaussian's.
+
 Regularisation (Sec. 3.1: the kernel is periodised by "a smooth transition" at
 the edges, after Potts-Steidl; the paper does not write it down). Reading: with
 a = 1/2 - eps_B the regularised radial profile is
@@ -36,8 +42,12 @@ from numpy.polynomial.hermite import hermval
 
 
 def kappa(r, ell: float, kind: str = "gauss"):
-    """kind='gauss': exp(-r^2/c^2); kind='der': (r^2/c^2) exp(-r^2/c^2); c = sqrt(2) ell."""
+    """kind='gauss': exp(-r^2/c^2); kind='der': (r^2/c^2) exp(-r^2/c^2); c = sqrt(2) ell;
+    kind='matern': exp(-r/ell); kind='matern_der': (r/ell) exp(-r/ell)."""
     r = np.asarray(r, dtype=np.float64)
+    if kind in ("matern", "matern_der"):
+        t = r / ell
+        return np.exp(-t) if kind == "matern" else t * np.exp(-t)
     q = r * r / (2.0 * ell * ell)
     e = np.exp(-q)
     return e if kind == "gauss" else q * e
@@ -48,7 +58,12 @@ def radial_derivatives(r0: float, ell: float, p: int, kind: str = "gauss"):
 
     Gaussian: d^j/dr^j exp(-(r/c)^2) = (-1/c)^j H_j(r/c) exp(-(r/c)^2), H_j the
     physicists' Hermite polynomials. Derivative kernel: Leibniz rule on
-    (r/c)^2 * exp(-(r/c)^2)."""
+    (r/c)^2 * exp(-(r/c)^2). Matern: d^j/dr^j exp(-r/ell) = (-1/ell)^j exp(-r/ell) and, by the same
+    rule, d^j/dr^j (r/ell) exp(-r/ell) = (-1/ell)^j exp(-r/ell) (r/ell - j)."""
+    if kind in ("matern", "matern_der"):
+        j = np.arange(p, dtype=np.float64)
+        g = (-1.0 / ell) ** j * np.exp(-r0 / ell)
+        return g if kind == "matern" else g * (r0 / ell - j)
     c = np.sqrt(2.0) * ell
     x = r0 / c
     g = []
