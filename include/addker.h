@@ -61,6 +61,18 @@ extern "C" {
 
 #define ADDKER_WIN_KB 0            /* Kaiser-Bessel window (the only one implemented) */
 
+/* Kernel families (addker_opts.kernel):
+ *   ADDKER_KERNEL_GAUSS     kappa_s(r) = exp(-r^2/(2 ell_s^2)), derivative kernel (r^2/(2 ell_s^2)) kappa_s,
+ *                           dK/d ell_s = sigma_f^2 (2/ell_s) K_s^der (Sec. 3.3)
+ *   ADDKER_KERNEL_MATERN12  kappa_s(r) = exp(-r/ell_s), derivative kernel (r/ell_s) kappa_s,
+ *                           dK/d ell_s = sigma_f^2 (1/ell_s) K_s^der (Sec. 5, "Extension to Other
+ *                           Kernels"). Same boundary regularisation; the kink at r = 0 is not corrected
+ *                           (the paper describes no near-field correction), so the Fourier error is
+ *                           far larger than the Gaussian's at equal M (e.g. 3e-3 at M = 32, 5e-4 at
+ *                           M = 64, relative, ell = 0.3). */
+#define ADDKER_KERNEL_GAUSS 0
+#define ADDKER_KERNEL_MATERN12 1
+
 typedef struct addker_plan addker_plan;
 
 /* Optional settings; pass NULL to addker_setup for the defaults. */
@@ -71,7 +83,7 @@ typedef struct {
     int    p;            /* regularisation degree (transition polynomial of degree 2p-1); -1 = default
                             max(1, floor(M eps_B + 1/2)); 0 = no regularisation (plain periodic continuation) */
     int    window;       /* ADDKER_WIN_KB */
-    int    reserved;     /* must be 0 */
+    int    kernel;       /* ADDKER_KERNEL_GAUSS (default) or ADDKER_KERNEL_MATERN12 */
     void*  stream;       /* cudaStream_t for every product of this plan; NULL = legacy default stream */
 } addker_opts;
 

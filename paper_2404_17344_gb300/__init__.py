@@ -53,8 +53,10 @@ class AddKer:
     bandwidth: M (int or per-window list), cutoff: window cutoff m.
     """
 
+    KERNELS = {"gauss": native.ADDKER_KERNEL_GAUSS, "matern": native.ADDKER_KERNEL_MATERN12}
+
     def __init__(self, points, windows, ell, sigma_f=1.0, bandwidth=32, cutoff=4, eps_B=1.0 / 16.0,
-                 p=-1, sigma_os=2.0):
+                 p=-1, sigma_os=2.0, kernel="gauss"):
         L = native.lib()
         pts = _dev_f32(points, "points")
         if pts.dim() != 2:
@@ -71,6 +73,9 @@ class AddKer:
         opts = native.addker_opts()
         native.check(L.addker_opts_default(ctypes.byref(opts)), "addker_opts_default")
         opts.sigma_os, opts.eps_B, opts.p = float(sigma_os), float(eps_B), int(p)
+        if kernel not in self.KERNELS:
+            raise ValueError(f"kernel must be one of {sorted(self.KERNELS)}")
+        opts.kernel = self.KERNELS[kernel]
         opts.stream = _stream_ptr()
         plan = ctypes.c_void_p()
         native.check(L.addker_setup(ctypes.byref(plan), ctypes.c_void_p(pts.data_ptr()), self.N, self.d, off, feat,
@@ -82,6 +87,7 @@ class AddKer:
         self.bandwidth = bw
         self.cutoff = int(cutoff)
         self.sigma_os = float(sigma_os)
+        self.kernel = kernel
 
     # -- plumbing ---------------------------------------------------------------------------
     def _ready(self):

@@ -141,14 +141,21 @@ __global__ void k_scatter(const float* __restrict__ X, int64_t N, int d, int f0,
 
 struct Transition {                      // T(r) = sum_i s[i] ((r - a)/h)^i on a < r <= 1/2
     int np;                              // 2p coefficients (0: no regularisation)
-    double s[2][32];                     // [kind][i], kind 0 Gaussian, 1 derivative kernel
+    int family;                          // ADDKER_KERNEL_GAUSS or ADDKER_KERNEL_MATERN12
+    double s[2][32];                     // [kind][i], kind 0 the kernel, 1 its derivative kernel
     double a, h, vb[2];
 };
 
-__device__ double kernel_value(double r, double ell, int kind)
+// Radial profiles (Sec. 3.3, eqs. "implement_gaussian_kernel", "implement_der_gaussian_kernel"; Sec. 5
+// for Matern(1/2)): Gaussian exp(-q), q = r^2/(2 ell^2), and q exp(-q); Matern exp(-t), t = r/ell, and
+// t exp(-t).
+__host__ __device__ inline double kernel_value(double r, double ell, int kind, int family)
 {
-    double q = r * r / (2.0 * ell * ell);
-    double e = exp(-q);
+    if (family == ADDKER_KERNEL_MATERN12) {
+        const double t = r / ell, e = exp(-t);
+        return kind == 0 ? e : t * e;
+    }
+    const double q = r * r / (2.0 * ell * ell), e = exp(-q);
     return kind == 0 ? e : q * e;
 }
 
@@ -171,7 +178,7 @@ __global__ void k_coef_sample(int M, double ell, Transition tr, double* __restri
     for (int kind = 0; kind < 2; ++kind) {
         double val;
         if (tr.np == 0 || r <= tr.a) {
-            val = kernel_value(r, ell, kind);
+            val = kernel_value(r, ell, kind, tr.family);
         } else if (r <= 0.5) {
             double sg = (r - tr.a) / tr.h, acc = 0.0;
             for (int i = tr.np - 1; i >= 0; --i) acc = acc * sg + tr.s[kind][i];
@@ -319,8 +326,17 @@ __global__ void k_scale(const float* __restrict__ X, int64_t n, float f, float* 
 // Taylor coefficients at r = a of the Gaussian (kind 0) or the derivative kernel (kind 1), orders
 // 0..p-1, by power-series arithmetic: exp(-(a+t)^2/c^2) = exp(-a^2/c^2) exp(q(t)),
 // q(t) = -(2 a t + t^2)/c^2, and E = exp(q) satisfies E' = q' E.
-void taylor_at(double a, double ell, int p, int kind, double* out)
+void taylor_at(double a, double ell, int p, int kind, int family, double* out)
 {
+    if (family == ADDKER_KERNEL_MATERN12) {
+        // k-th Taylor coefficient at a: (-1/ell)^k e^{-a/ell} / k!, times (a/ell - k) for t e^{-t}
+        double f = std::exp(-a / ell);
+        for (int k = 0; k < p; ++k) {
+            out[k] = kind == 0 ? f : f * (a / ell - k);
+            f *= -1.0 / (ell * (k + 1));
+        }
+        return;
+    }
     double c2 = 2.0 * ell * ell;
     double q1 = -2.0 * a / c2, q2 = -1.0 / c2;
     std::vector<double> e(p + 2, 0.0);
@@ -342,21 +358,19 @@ void taylor_at(double a, double ell, int p, int kind, double* out)
 
 // Transition polynomial of degree 2p-1 on [a, 1/2] (in sigma = (r - a)/h): matches the kernel's
 // first p Taylor coefficients at a, the value kernel(1/2) at 1/2 and p-1 vanishing derivatives there.
-int make_transition(double ell, int p, double eps_B, Transition* tr)
+int make_transition(double ell, int p, double eps_B, int family, Transition* tr)
 {
     std::memset(tr, 0, sizeof(*tr));
     tr->a = 0.5 - eps_B;
     tr->h = eps_B;
-    for (int kind = 0; kind < 2; ++kind) {
-        double q = 0.125 / (ell * ell);
-        tr->vb[kind] = kind == 0 ? std::exp(-q) : q * std::exp(-q);
-    }
+    tr->family = family;
+    for (int kind = 0; kind < 2; ++kind) tr->vb[kind] = kernel_value(0.5, ell, kind, family);
     if (p == 0) return ADDKER_OK;
     if (p > 12) return ADDKER_EINVAL;
     tr->np = 2 * p;
     for (int kind = 0; kind < 2; ++kind) {
         double t[16];
-        taylor_at(tr->a, ell, p, kind, t);
+        taylor_at(tr->a, ell, p, kind, family, t);
         double* s = tr->s[kind];
         for (int i = 0; i < p; ++i) s[i] = t[i] * std::pow(tr->h, i);
         // equations j = 0..p-1 at sigma = 1: sum_i ff(i, j) s_i = (j == 0 ? vb : 0), ff = falling factorial
@@ -502,7 +516,7 @@ int compute_multipliers(Plan& p, int s)
     // default degree: M eps_B rounded half up, at least 1
     int ps = p.p_opt >= 0 ? p.p_opt : std::max(1, (int)std::floor(w.M * p.eps_B + 0.5));
     Transition tr;
-    CS(make_transition(p.ell[s], ps, p.eps_B, &tr));
+    CS(make_transition(p.ell[s], ps, p.eps_B, p.kernel, &tr));
     int64_t total = 1;
     for (int t = 0; t < w.D; ++t) total *= w.M;
     double *a = nullptr, *b = nullptr, *c = nullptr, *d = nullptr, *ph = nullptr;
@@ -542,13 +556,16 @@ int compute_multipliers(Plan& p, int s)
     return ADDKER_OK;
 }
 
+// dK/d ell_s = sigma_f^2 (f / ell_s) K_s^der: f = 2 for the Gaussian (Sec. 3.3), 1 for Matern(1/2) (Sec. 5)
+double der_factor(const Plan& p) { return p.kernel == ADDKER_KERNEL_MATERN12 ? 1.0 : 2.0; }
+
 int upload_scales(Plan& p)
 {
     std::vector<float> sc(3 * p.P);
     for (int s = 0; s < p.P; ++s) {
         sc[s] = 1.0f;
         sc[p.P + s] = (float)(p.sigma_f * p.sigma_f);
-        sc[2 * p.P + s] = (float)(p.sigma_f * p.sigma_f * 2.0 / p.ell[s]);
+        sc[2 * p.P + s] = (float)(p.sigma_f * p.sigma_f * der_factor(p) / p.ell[s]);
     }
     CK(cudaMemcpy(p.scale_dev, sc.data(), sizeof(float) * sc.size(), cudaMemcpyHostToDevice));
     return ADDKER_OK;
@@ -953,7 +970,7 @@ int multipliers_with_scratch(const WinDev& w, double ell, int p_opt, double eps_
 {
     const int ps = p_opt >= 0 ? p_opt : std::max(1, (int)std::floor(w.M * eps_B + 0.5));
     Transition tr;
-    CS(make_transition(ell, ps, eps_B, &tr));
+    CS(make_transition(ell, ps, eps_B, ADDKER_KERNEL_GAUSS, &tr));
     int64_t total = 1;
     for (int t = 0; t < w.D; ++t) total *= w.M;
     double* a = scratch;
@@ -1027,7 +1044,7 @@ int addker_opts_default(addker_opts* o)
     o->eps_B = 1.0 / 16.0;
     o->p = -1;
     o->window = ADDKER_WIN_KB;
-    o->reserved = 0;
+    o->kernel = ADDKER_KERNEL_GAUSS;
     o->stream = nullptr;
     return ADDKER_OK;
 }
@@ -1042,7 +1059,9 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
     if (opts) o = *opts;
     if (N < 1 || N > 0x7fffffffLL || d < 1 || P < 1 || P > kMaxWindows || !win_off || !win_feat || !ell || !bandwidth)
         return ADDKER_EINVAL;
-    if (!(sigma_f > 0.0) || cutoff < 2 || cutoff > 8 || o.window != ADDKER_WIN_KB || o.reserved != 0) return ADDKER_EINVAL;
+    if (!(sigma_f > 0.0) || cutoff < 2 || cutoff > 8 || o.window != ADDKER_WIN_KB ||
+        (o.kernel != ADDKER_KERNEL_GAUSS && o.kernel != ADDKER_KERNEL_MATERN12))
+        return ADDKER_EINVAL;
     if (!(o.eps_B > 0.0 && o.eps_B < 0.5) || !(o.sigma_os >= 1.25 && o.sigma_os <= 4.0) || o.p < -1 || o.p > 12)
         return ADDKER_EINVAL;
     if (win_off[0] != 0) return ADDKER_EINVAL;
@@ -1073,6 +1092,7 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
     p.sigma_os = o.sigma_os;
     p.eps_B = o.eps_B;
     p.p_opt = o.p;
+    p.kernel = o.kernel;
     p.stream = static_cast<cudaStream_t>(o.stream);
     p.feat_off.assign(win_off, win_off + P + 1);
     p.feat.assign(win_feat, win_feat + win_off[P]);
@@ -1290,7 +1310,7 @@ int addker_vjp(addker_plan* plan, const float* v, const float* w, float* grad_v,
         }
     }
     ThetaScale sc;
-    for (int s = 0; s < p.P; ++s) sc.s[s] = p.sigma_f * p.sigma_f * 2.0 / p.ell[s];
+    for (int s = 0; s < p.P; ++s) sc.s[s] = p.sigma_f * p.sigma_f * der_factor(p) / p.ell[s];
     sc.s[p.P] = 2.0 * p.sigma_f;
     launch_k(true, k_theta_grad, dim3(1), dim3(64), 0, st, (const double*)p.dots, p.P, sc, grad_theta);
     CK(cudaGetLastError());

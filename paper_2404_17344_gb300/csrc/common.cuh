@@ -75,6 +75,7 @@ struct Plan {
     int d = 0, P = 0, m = 4;
     double sigma_f = 1.0, sigma_os = 2.0, eps_B = 1.0 / 16.0;
     int p_opt = -1;
+    int kernel = ADDKER_KERNEL_GAUSS;     // radial profile family (addker_opts.kernel)
     cudaStream_t stream = nullptr;
     std::vector<int> dims, bandwidth, feat_off, feat;
     std::vector<double> ell;

@@ -21,6 +21,8 @@ ADDKER_ELIMIT = -6
 ADDKER_ELL_SHARED = -1
 ADDKER_SIGMA_F = -2
 ADDKER_WIN_KB = 0
+ADDKER_KERNEL_GAUSS = 0
+ADDKER_KERNEL_MATERN12 = 1
 
 
 def ADDKER_ELL(s: int) -> int:
@@ -29,7 +31,7 @@ def ADDKER_ELL(s: int) -> int:
 
 class addker_opts(ctypes.Structure):
     _fields_ = [("sigma_os", ctypes.c_double), ("eps_B", ctypes.c_double), ("p", ctypes.c_int),
-                ("window", ctypes.c_int), ("reserved", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("window", ctypes.c_int), ("kernel", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 # name -> (restype, argtypes); every entry point of include/addker.h

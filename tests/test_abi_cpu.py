@@ -45,7 +45,8 @@ def test_status_codes_match_header():
     from paper_2404_17344_gb300 import native
     text = open(HEADER).read()
     for name in ("ADDKER_OK", "ADDKER_EINVAL", "ADDKER_EDOMAIN", "ADDKER_ENOMEM", "ADDKER_ECUDA",
-                 "ADDKER_ETIMEOUT", "ADDKER_ELIMIT", "ADDKER_ELL_SHARED", "ADDKER_SIGMA_F", "ADDKER_WIN_KB"):
+                 "ADDKER_ETIMEOUT", "ADDKER_ELIMIT", "ADDKER_ELL_SHARED", "ADDKER_SIGMA_F", "ADDKER_WIN_KB",
+                 "ADDKER_KERNEL_GAUSS", "ADDKER_KERNEL_MATERN12"):
         m = re.search(rf"#define {name}\s+\(?(-?\d+)\)?", text)
         assert m and int(m.group(1)) == getattr(native, name), name
 
@@ -56,7 +57,7 @@ def test_strerror_and_defaults(lib):
         assert isinstance(lib.addker_strerror(code), bytes)
     o = native.addker_opts()
     assert lib.addker_opts_default(ctypes.byref(o)) == 0
-    assert o.sigma_os == 2.0 and o.eps_B == 1 / 16 and o.p == -1
+    assert o.sigma_os == 2.0 and o.eps_B == 1 / 16 and o.p == -1 and o.kernel == native.ADDKER_KERNEL_GAUSS
     assert lib.addker_opts_default(None) == native.ADDKER_EINVAL
     assert lib.addker_free(None) == 0
 
@@ -113,3 +114,18 @@ def test_product_path_has_no_cpu_fallback():
             src = open(os.path.join(pkg, f)).read()
             assert "oracle" not in src.replace("the oracle", ""), f
             assert "workloads" not in src, f
+
+
+def test_setup_rejects_unknown_kernel_family(lib):
+    from paper_2404_17344_gb300 import native
+    o = native.addker_opts()
+    lib.addker_opts_default(ctypes.byref(o))
+    o.kernel = 7
+    plan = ctypes.c_void_p()
+    off = (ctypes.c_int * 2)(0, 3)
+    feat = (ctypes.c_int * 3)(0, 1, 2)
+    ell = (ctypes.c_double * 1)(0.5)
+    bw = (ctypes.c_int * 1)(32)
+    st = lib.addker_setup(ctypes.byref(plan), ctypes.c_void_p(0x1000), 10, 3, off, feat, 1, ell, 1.0, bw, 4,
+                          ctypes.byref(o))
+    assert st == native.ADDKER_EINVAL and not plan.value

@@ -1,0 +1,84 @@
+"""The additive Matern(1/2) kernel (Sec. 5, "Extension to Other Kernels") on the GPU against the FP64
+oracle with identical settings (same regularisation, window and bandwidth): 1e-5 relative L2, as for
+the Gaussian. Against the direct sums the method's own Fourier error dominates (the kernel's kink at
+r = 0 is not corrected); the GPU stays within that error plus 1e-5."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import fastsum
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch
+
+
+def make_op(torch, wl):
+    from paper_2404_17344_gb300 import AddKer
+    return AddKer(torch.from_numpy(wl.points).cuda(), wl.windows, wl.ell, wl.sigma_f, wl.bandwidth, wl.cutoff,
+                  kernel="matern")
+
+
+@pytest.mark.parametrize("cfg,N", [("c1", 5000), ("c3", 3000)])
+def test_matern_products_match_oracle(torch_cuda, cfg, N):
+    from paper_2404_17344_gb300 import ADDKER_ELL
+    torch = torch_cuda
+    wl = workloads.make(cfg, N=N)
+    wl.sigma_f = 1.2
+    v = wl.vector()
+    op = make_op(torch, wl)
+    Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
+    Kr, dKr = fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f, v.astype(np.float64), wl.bandwidth,
+                                 wl.cutoff, kernel="matern")
+    assert rel(Kv.cpu(), Kr) < TOL
+    for s in range(wl.P):
+        assert rel(dK[s].cpu(), dKr[s]) < TOL, s
+        assert rel(op.dmatvec(ADDKER_ELL(s), torch.from_numpy(v).cuda()).cpu(), dKr[s]) < TOL, s
+
+
+def test_matern_against_direct_sums(torch_cuda):
+    torch = torch_cuda
+    wl = workloads.make("c1", N=4000)
+    v = wl.vector()
+    op = make_op(torch, wl)
+    Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
+    rows = np.random.default_rng(5).choice(wl.N, 300, replace=False)
+    Kd, dKd = fastsum.direct_matern(wl.points, wl.windows, wl.ell, wl.sigma_f, v, rows=rows)
+    Kn, dKn = fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f, v.astype(np.float64), wl.bandwidth,
+                                 wl.cutoff, kernel="matern", rows=rows)
+    assert rel(Kv.cpu().numpy()[rows], Kd) <= rel(Kn, Kd) + TOL
+    for s in range(wl.P):
+        assert rel(dK[s].cpu().numpy()[rows], dKd[s]) <= rel(dKn[s], dKd[s]) + TOL
+
+
+def test_matern_vjp_length_scale_gradient(torch_cuda):
+    """The vector-Jacobian product's length-scale gradients use the Matern factor 1/ell_s: they equal
+    w^T (dK/d ell_s v) from the fused product."""
+    torch = torch_cuda
+    wl = workloads.make("c2", N=3000)
+    v, w = wl.vector(), wl.vector(which=2)
+    op = make_op(torch, wl)
+    _, gt, _ = op.vjp(torch.from_numpy(v).cuda(), torch.from_numpy(w).cuda())
+    Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
+    w64 = w.astype(np.float64)
+    for s in range(wl.P):
+        ref = w64 @ dK[s].cpu().numpy().astype(np.float64)
+        assert abs(float(gt[s]) - ref) <= TOL * np.abs(w64) @ np.abs(dK[s].cpu().numpy())
+    ref_sf = (2.0 / wl.sigma_f) * (w64 @ Kv.cpu().numpy().astype(np.float64))
+    assert abs(float(gt[wl.P]) - ref_sf) <= TOL * (2.0 / wl.sigma_f) * (np.abs(w64) @ np.abs(Kv.cpu().numpy()))
