@@ -314,6 +314,23 @@ __global__ void k_max_norm(const float* __restrict__ X, int64_t N, int d, const 
     if ((threadIdx.x & 31) == 0) atomicMax(result, __float_as_uint(best));
 }
 
+// dst[i] = src[i], i < n, where one side may be page-locked host memory reached over the CPU-GPU
+// link: every SM streams 16-byte words, which moves more than one copy engine does.
+__global__ void k_copy(const float* __restrict__ src, float* __restrict__ dst, int64_t n, int vec)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t done = 0;
+    if (vec) {
+        const int64_t n4 = n / 4;
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        for (int64_t k = i; k < n4; k += stride) d4[k] = s4[k];
+        done = 4 * n4;
+    }
+    for (int64_t k = done + i; k < n; k += stride) dst[k] = src[k];
+}
+
 __global__ void k_scale(const float* __restrict__ X, int64_t n, float f, float* __restrict__ Y)
 {
     grid_dep_wait();
@@ -1329,10 +1346,37 @@ int addker_matvec_all_host(addker_plan* plan, const float* v, float* Kv, float* 
         p.stage_cap = need;
     }
     cudaStream_t st = p.stream;
-    CK(cudaMemcpyAsync(p.stage_v, v, sizeof(float) * need, cudaMemcpyHostToDevice, st));
+    // page-locked host buffers are read and written by copy kernels over the CPU-GPU link (more
+    // bandwidth than one copy engine); pageable ones go through cudaMemcpyAsync
+    auto mapped = [](const void* q) -> void* {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+    };
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int cb = 4 * std::max(sms, 1);
+    auto copy = [&](const float* src, float* dst, int64_t n) {
+        const int vec = (reinterpret_cast<uintptr_t>(src) % 16 == 0) && (reinterpret_cast<uintptr_t>(dst) % 16 == 0);
+        k_copy<<<cb, 256, 0, st>>>(src, dst, n, vec);
+        return cudaGetLastError();
+    };
+    const float* vm = static_cast<const float*>(mapped(v));
+    float* Km = static_cast<float*>(mapped(Kv));
+    float* Dm = dKdell ? static_cast<float*>(mapped(dKdell)) : nullptr;
+    if (vm) CK(copy(vm, p.stage_v, need));
+    else CK(cudaMemcpyAsync(p.stage_v, v, sizeof(float) * need, cudaMemcpyHostToDevice, st));
     CS(addker_matvec_all(plan, p.stage_v, p.stage_k, dKdell ? p.stage_d : nullptr, nrhs));
-    CK(cudaMemcpyAsync(Kv, p.stage_k, sizeof(float) * need, cudaMemcpyDeviceToHost, st));
-    if (dKdell) CK(cudaMemcpyAsync(dKdell, p.stage_d, sizeof(float) * need * p.P, cudaMemcpyDeviceToHost, st));
+    if (Km) CK(copy(p.stage_k, Km, need));
+    else CK(cudaMemcpyAsync(Kv, p.stage_k, sizeof(float) * need, cudaMemcpyDeviceToHost, st));
+    if (dKdell) {
+        if (Dm) CK(copy(p.stage_d, Dm, need * p.P));
+        else CK(cudaMemcpyAsync(dKdell, p.stage_d, sizeof(float) * need * p.P, cudaMemcpyDeviceToHost, st));
+    }
     CK(cudaStreamSynchronize(st));
     return ADDKER_OK;
 }
