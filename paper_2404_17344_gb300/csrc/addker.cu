@@ -745,23 +745,38 @@ int vec_ok(const Plan& p, const float* out, int64_t ld)
 // The chunk is the scheduling grain of the spread and gather kernels (addker_autotune chooses it).
 int build_items(Plan& p, int chunk)
 {
-    std::vector<int4> lists[kKinds];
-    for (int k = 0; k < kKinds; ++k) p.item_begin[k].assign(1, 0);
+    // two lists: the one every kernel uses, and the spread's, which differs for 2-D windows only
+    std::vector<int4> lists[2][kKinds];
+    for (int k = 0; k < kKinds; ++k) {
+        p.item_begin[k].assign(1, 0);
+        p.item_begin_sp[k].assign(1, 0);
+    }
     for (int s = 0; s < p.P; ++s) {
-        std::vector<int4> items;
-        for (const int4& c : p.cells[s])
-            for (int st = 0; st < c.y; st += chunk) items.push_back(make_int4(c.x + st, std::min(chunk, c.y - st), c.z, s));
-        std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) { return a.y > b.y; });
-        std::vector<int4>& dst = lists[p.kind[s]];
-        dst.insert(dst.end(), items.begin(), items.end());
-        for (int k = 0; k < kKinds; ++k) p.item_begin[k].push_back((int)lists[k].size());
+        for (int l = 0; l < 2; ++l) {
+            // spreading a 2-D window: few crowded cells whose 8x8 boxes overlap, so every item ends with
+            // atomic adds to the same few hundred grid values; those items are kLowdChunkFactor times
+            // larger (1-D windows, and the gathers, need the parallelism of small items more)
+            const int ch = (l == 1 && p.dims[s] == 2) ? chunk * kLowdChunkFactor : chunk;
+            std::vector<int4> items;
+            for (const int4& c : p.cells[s])
+                for (int st = 0; st < c.y; st += ch)
+                    items.push_back(make_int4(c.x + st, std::min(ch, c.y - st), c.z, s));
+            std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) { return a.y > b.y; });
+            std::vector<int4>& dst = lists[l][p.kind[s]];
+            dst.insert(dst.end(), items.begin(), items.end());
+        }
+        for (int k = 0; k < kKinds; ++k) {
+            p.item_begin[k].push_back((int)lists[0][k].size());
+            p.item_begin_sp[k].push_back((int)lists[1][k].size());
+        }
     }
     std::vector<int4> all;
-    for (int k = 0; k < kKinds; ++k) {
-        const int base = (int)all.size();
-        for (int& b : p.item_begin[k]) b += base;
-        all.insert(all.end(), lists[k].begin(), lists[k].end());
-    }
+    for (int l = 0; l < 2; ++l)
+        for (int k = 0; k < kKinds; ++k) {
+            const int base = (int)all.size();
+            for (int& b : (l == 0 ? p.item_begin[k] : p.item_begin_sp[k])) b += base;
+            all.insert(all.end(), lists[l][k].begin(), lists[l][k].end());
+        }
     if ((int64_t)all.size() > p.items_cap) {
         if (p.items) cudaFree(p.items);
         p.items = nullptr;

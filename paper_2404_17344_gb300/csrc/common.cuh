@@ -29,6 +29,7 @@ constexpr int kMaxRhsChunk = 8;         // right-hand sides processed together b
 enum { kKindFast3 = 0, kKindLow1 = 1, kKindLow2 = 2, kKindGen1 = 3, kKindGen2 = 4, kKindGen3 = 5, kKinds = 6 };
 inline int kind_of(int D, int m) { return m == 4 ? (D == 3 ? kKindFast3 : D) : 2 + D; }
 constexpr int kItemPoints = 256;        // default points per work item (one warp); see build_items
+constexpr int kLowdChunkFactor = 8;     // spread items of 2-D windows hold this many times more points
 constexpr int kMaxBandwidth = 64;
 
 // Piecewise polynomial form of the window used by every spreading/interpolation kernel: for a
@@ -89,6 +90,7 @@ struct Plan {
     int chunk = kItemPoints;              // points per work item at most
     std::vector<std::vector<int4>> cells; // per window: non-empty cells (first point, count, packed cell, s)
     std::vector<int> item_begin[kKinds];
+    std::vector<int> item_begin_sp[kKinds]; // the spread's list (larger items for 2-D windows), same array
     std::vector<int> kind;
     int slots = 0;                        // right-hand-side slots allocated per window
     std::vector<void*> slot_allocs;       // grid, h, buf1, buf2 of all slots (re-made when slots grow)

@@ -332,7 +332,8 @@ __host__ __device__ inline size_t small_front(int b0, int b1, int M, int D)
 }
 
 template <int D>
-__global__ void __launch_bounds__(kT) k_small_transform(const WinDev* __restrict__ wins, int w0, int spec_only)
+__global__ void __launch_bounds__(kT) k_small_transform(const WinDev* __restrict__ wins, int w0, int spec_only,
+                                                        int smem_bytes)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const WinDev& W = wins[w0 + blockIdx.x];
@@ -342,14 +343,24 @@ __global__ void __launch_bounds__(kT) k_small_transform(const WinDev* __restrict
     const int MD = D == 2 ? M * M : M;
     float* grid = W.grid + r * W.gsz;
     float2* h = W.h + r * W.gsz;
-    const float2* tf0 = W.twf[0];
-    const float2* tf1 = W.twf[1];
     // gs, t and G are dead once S is written, so B reuses their space (see small_smem)
     float* gs = reinterpret_cast<float*>(smem);                                   // b0 * b1
     float2* t = reinterpret_cast<float2*>(smem + sizeof(float) * ((b0 * b1 + 3) & ~3));   // b0 * M (D = 2)
     float2* G = t + (D == 2 ? b0 * M : 0);                                       // MD
     float4* B = reinterpret_cast<float4*>(smem);                                 // b0 * M (D = 2)
     float4* S = reinterpret_cast<float4*>(smem + small_front(b0, b1, M, D));     // MD
+    // the twiddles go to shared memory too when the launch provided room (every pass reads them
+    // b0 or M times; from global memory each pass would wait on L2 per term)
+    float2* tws = reinterpret_cast<float2*>(S + MD);
+    const bool stw = small_front(b0, b1, M, D) + sizeof(float4) * MD + sizeof(float2) * (b0 + (D == 2 ? b1 : 0)) * M <=
+                     (size_t)smem_bytes;
+    if (stw) {
+        for (int i = threadIdx.x; i < b0 * M; i += kT) cp_async8(tws + i, W.twf[0] + i);
+        if (D == 2)
+            for (int i = threadIdx.x; i < b1 * M; i += kT) cp_async8(tws + b0 * M + i, W.twf[1] + i);
+    }
+    const float2* tf0 = stw ? tws : W.twf[0];
+    const float2* tf1 = stw ? tws + b0 * M : W.twf[1];
     grid_dep_wait();
     for (int i = threadIdx.x; i < b0 * b1; i += kT) cp_async4(gs + i, grid + i);
     cp_async_wait_all();
@@ -433,11 +444,15 @@ __global__ void __launch_bounds__(kT) k_small_transform(const WinDev* __restrict
     }
 }
 
+// Shared memory of k_small_transform for window w: the passes' buffers, plus the twiddles when that
+// stays within 160 KB (the kernel checks the launch size itself).
 size_t small_smem(const WinDev& w)
 {
     const int b0 = w.box[0], b1 = w.D == 2 ? w.box[1] : 1, M = w.M;
     const int MD = w.D == 2 ? M * M : M;
-    return small_front(b0, b1, M, w.D) + sizeof(float4) * MD;
+    const size_t base = small_front(b0, b1, M, w.D) + sizeof(float4) * MD;
+    const size_t with_tw = base + sizeof(float2) * (b0 + (w.D == 2 ? b1 : 0)) * M;
+    return with_tw <= 160 * 1024 ? with_tw : base;
 }
 
 }  // namespace
@@ -498,7 +513,7 @@ cudaError_t launch_transforms(const Plan& p, int window, int nrhs, cudaStream_t 
     for (int D = 1; D <= 2; ++D) {
         if (sm[D] == 0) continue;
         launch_k(true, D == 1 ? k_small_transform<1> : k_small_transform<2>, dim3(hi - lo, nrhs), dim3(kT), sm[D],
-                 st, (const WinDev*)p.wins_dev, lo, spec_only ? 1 : 0);
+                 st, (const WinDev*)p.wins_dev, lo, spec_only ? 1 : 0, (int)sm[D]);
         ++n;
     }
     if (count) *count = n;
@@ -518,9 +533,9 @@ cudaError_t launch_transforms_window(const WinDev& w, const WinDev* w_dev, cudaS
         k_xround<<<g2, kT3, f3[1], st>>>(w_dev, 0, 0);
         k_inv_yz<<<g1, kT3, f3[2], st>>>(w_dev, 0);
     } else if (w.D == 2) {
-        k_small_transform<2><<<dim3(1, 1), kT, small_smem(w), st>>>(w_dev, 0, 0);
+        k_small_transform<2><<<dim3(1, 1), kT, small_smem(w), st>>>(w_dev, 0, 0, (int)small_smem(w));
     } else {
-        k_small_transform<1><<<dim3(1, 1), kT, small_smem(w), st>>>(w_dev, 0, 0);
+        k_small_transform<1><<<dim3(1, 1), kT, small_smem(w), st>>>(w_dev, 0, 0, (int)small_smem(w));
     }
     return cudaGetLastError();
 }

@@ -354,27 +354,42 @@ __global__ void __launch_bounds__(kWarps * 32) k_spread_lowd_w8(const int4* __re
     float acc[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.f;
-    for (int k = lane; k < it.y; k += 32) {
-        const float4 p = pts[k];
-        const float vv = __ldg(v + __float_as_int(p.w));
-        float wx[W];
-        int c;
-        window_weights<W>(poly, p.x, P.n, wx, &c);
-        if (D == 1) {
+    // U points per lane per round, their loads issued together (the work per point is small, so one
+    // point at a time would leave the loop waiting on memory); points past the item weigh 0
+    constexpr int U = 4;
+    for (int k0 = lane; k0 < it.y; k0 += 32 * U) {
+        float4 p[U];
+        float vv[U];
 #pragma unroll
-            for (int a = 0; a < W; ++a) acc[a] = fmaf(vv, wx[a], acc[a]);
-        } else {
-            float wy[W];
-            window_weights<W>(poly, p.y, P.n, wy, &c);
+        for (int u = 0; u < U; ++u) p[u] = pts[min(k0 + 32 * u, it.y - 1)];
 #pragma unroll
-            for (int a = 0; a < W; ++a) {
-                const float xa = vv * wx[a];
+        for (int u = 0; u < U; ++u) vv[u] = k0 + 32 * u < it.y ? __ldg(v + __float_as_int(p[u].w)) : 0.f;
+        // one point at a time (the arrays rotate so that indices stay static and in registers)
+#pragma unroll 1
+        for (int u = 0; u < U; ++u) {
+            const float4 pu = p[0];
+            const float vu = vv[0];
 #pragma unroll
-                for (int b = 0; b < W; b += 2) {
-                    float2 t = make_float2(acc[a * W + b], acc[a * W + b + 1]);
-                    t = __ffma2_rn(make_float2(xa, xa), make_float2(wy[b], wy[b + 1]), t);
-                    acc[a * W + b] = t.x;
-                    acc[a * W + b + 1] = t.y;
+            for (int z = 0; z < U - 1; ++z) { p[z] = p[z + 1]; vv[z] = vv[z + 1]; }
+            float wx[W];
+            int c;
+            window_weights<W>(poly, pu.x, P.n, wx, &c);
+            if (D == 1) {
+#pragma unroll
+                for (int a = 0; a < W; ++a) acc[a] = fmaf(vu, wx[a], acc[a]);
+            } else {
+                float wy[W];
+                window_weights<W>(poly, pu.y, P.n, wy, &c);
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    const float xa = vu * wx[a];
+#pragma unroll
+                    for (int b = 0; b < W; b += 2) {
+                        float2 t = make_float2(acc[a * W + b], acc[a * W + b + 1]);
+                        t = __ffma2_rn(make_float2(xa, xa), make_float2(wy[b], wy[b + 1]), t);
+                        acc[a * W + b] = t.x;
+                        acc[a * W + b + 1] = t.y;
+                    }
                 }
             }
         }
@@ -425,34 +440,45 @@ __global__ void __launch_bounds__(kWarps * 32) k_gather_lowd_w8(const int4* __re
     const float4* __restrict__ pts = P.pts + it.x;
     const float sK = WK ? scaleK[it.w] : 0.f;
     const float sD = WD ? scaleD[it.w] : 0.f;
-    for (int k = lane; k < it.y; k += 32) {
-        const float4 p = pts[k];
-        float wx[W];
-        int c;
-        window_weights<W>(poly, p.x, P.n, wx, &c);
-        float2 f = make_float2(0.f, 0.f);
-        if (D == 1) {
+    constexpr int U = 4;                                       // points per lane per round, loads together
+    for (int k0 = lane; k0 < it.y; k0 += 32 * U) {
+        float4 pp[U];
 #pragma unroll
-            for (int a = 0; a < W; ++a) f = __ffma2_rn(t[a], make_float2(wx[a], wx[a]), f);
-        } else {
-            float wy[W];
-            window_weights<W>(poly, p.y, P.n, wy, &c);
+        for (int q = 0; q < U; ++q) pp[q] = pts[min(k0 + 32 * q, it.y - 1)];
+        // one point at a time (the array rotates so that indices stay static and in registers)
+#pragma unroll 1
+        for (int q = 0; q < U; ++q) {
+            if (k0 + 32 * q >= it.y) break;
+            const float4 p = pp[0];
 #pragma unroll
-            for (int a = 0; a < W; ++a) {
-                float2 u = make_float2(0.f, 0.f);
-                const float4* row = reinterpret_cast<const float4*>(t + a * W);
+            for (int z = 0; z < U - 1; ++z) pp[z] = pp[z + 1];
+            float wx[W];
+            int c;
+            window_weights<W>(poly, p.x, P.n, wx, &c);
+            float2 f = make_float2(0.f, 0.f);
+            if (D == 1) {
 #pragma unroll
-                for (int b = 0; b < W; b += 2) {
-                    const float4 hv = row[b / 2];
-                    u = __ffma2_rn(make_float2(hv.x, hv.y), make_float2(wy[b], wy[b]), u);
-                    u = __ffma2_rn(make_float2(hv.z, hv.w), make_float2(wy[b + 1], wy[b + 1]), u);
+                for (int a = 0; a < W; ++a) f = __ffma2_rn(t[a], make_float2(wx[a], wx[a]), f);
+            } else {
+                float wy[W];
+                window_weights<W>(poly, p.y, P.n, wy, &c);
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    float2 u = make_float2(0.f, 0.f);
+                    const float4* row = reinterpret_cast<const float4*>(t + a * W);
+#pragma unroll
+                    for (int b = 0; b < W; b += 2) {
+                        const float4 hv = row[b / 2];
+                        u = __ffma2_rn(make_float2(hv.x, hv.y), make_float2(wy[b], wy[b]), u);
+                        u = __ffma2_rn(make_float2(hv.z, hv.w), make_float2(wy[b + 1], wy[b + 1]), u);
+                    }
+                    f = __ffma2_rn(u, make_float2(wx[a], wx[a]), f);
                 }
-                f = __ffma2_rn(u, make_float2(wx[a], wx[a]), f);
             }
+            const int64_t i = (int64_t)__float_as_int(p.w);
+            if (WK) outK[i + it.w * strideK + r * rstrideK] = sK * f.x;
+            if (WD) outD[i + it.w * strideD + r * rstrideD] = sD * f.y;
         }
-        const int64_t i = (int64_t)__float_as_int(p.w);
-        if (WK) outK[i + it.w * strideK + r * rstrideK] = sK * f.x;
-        if (WD) outD[i + it.w * strideD + r * rstrideD] = sD * f.y;
     }
 }
 
@@ -579,9 +605,9 @@ static int resident_blocks(K kernel, int threads)
 }
 
 // Items of one kind for one window, or for all windows (window < 0).
-static void item_range(const Plan& p, int kind, int window, int* lo, int* hi)
+static void item_range(const Plan& p, int kind, int window, int* lo, int* hi, bool spread = false)
 {
-    const std::vector<int>& b = p.item_begin[kind];
+    const std::vector<int>& b = spread ? p.item_begin_sp[kind] : p.item_begin[kind];
     if (window < 0) { *lo = b.front(); *hi = b.back(); }
     else { *lo = b[window]; *hi = b[window + 1]; }
 }
@@ -594,7 +620,7 @@ cudaError_t launch_spread(const Plan& p, int window, const float* v, int64_t ldv
     const WinDev* wd = p.wins_dev;
     for (int k = 0; k < kKinds; ++k) {
         int lo, hi;
-        item_range(p, k, window, &lo, &hi);
+        item_range(p, k, window, &lo, &hi, true);
         if (hi <= lo) continue;
         const int n = hi - lo;
         const int4* it = p.items + lo;
