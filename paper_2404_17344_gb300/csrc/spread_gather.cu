@@ -175,23 +175,15 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_spread3_w8(const int4* __res
     }
 }
 
-// Contraction of the staged box t4 with NP points per lane: points k and k + 32 (NP = 2, the second
-// only if k + 32 < count). The pair (h^K, h^D) of a grid point is multiplied by duplicated weights in
-// one packed FMA.
+// Contraction of the staged box t4 with NP points per lane, p[i] written out where has[i]. The pair
+// (h^K, h^D) of a grid point is multiplied by duplicated weights in one packed FMA.
 template <int NP, bool WK, bool WD>
-__device__ __forceinline__ void gather_points(const float4* t4, const float4* __restrict__ pts, int k, int count,
-                                              int n, const WinPoly& poly, float* __restrict__ outK,
+__device__ __forceinline__ void gather_points(const float4* t4, const float4 (&p)[2], const bool (&has)[2], int n,
+                                              const WinPoly& poly, float* __restrict__ outK,
                                               float* __restrict__ outD, float sK, float sD, int64_t offK,
                                               int64_t offD)
 {
     constexpr int W = 8;
-    float4 p[NP];
-    bool has[NP];
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-        has[i] = k + 32 * i < count;
-        p[i] = pts[has[i] ? k + 32 * i : k];
-    }
     float x[NP][W];
     float2 y[NP][W], z[NP][W];
 #pragma unroll
@@ -274,6 +266,12 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_gather3_w8(const int4* __res
     const int sy = P.box[2], sx = P.box[1] * P.box[2];
     const int r = blockIdx.y;                                  // right-hand side
     const float2* __restrict__ h = P.h + r * P.gsz + (size_t)ox * sx + (size_t)oy * sy + oz;
+    const float4* __restrict__ pts = P.pts + it.x;
+    const int count = it.y;
+    // the first round's points load while the box is staged; each round loads the next round's
+    float4 pa[2];
+    pa[0] = pts[min(lane, count - 1)];
+    pa[1] = pts[min(lane + 32, count - 1)];
     float2* t = tile[warp];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
@@ -283,17 +281,24 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_gather3_w8(const int4* __res
     }
     __syncwarp();
     const float4* t4 = reinterpret_cast<const float4*>(t);
-    const float4* __restrict__ pts = P.pts + it.x;
     const float sK = WK ? scaleK[it.w] : 0.f;
     const float sD = WD ? scaleD[it.w] : 0.f;
     const int n = P.n;
     // two points per lane while more than 32 remain, then one, so tail lanes do no dead work
     const int64_t offK = it.w * strideK + r * rstrideK, offD = it.w * strideD + r * rstrideD;
-    int base = 0;
-    for (; it.y - base > 32; base += 64)
-        gather_points<2, WK, WD>(t4, pts, base + lane, it.y, n, poly, outK, outD, sK, sD, offK, offD);
-    if (base < it.y && base + lane < it.y)
-        gather_points<1, WK, WD>(t4, pts, base + lane, it.y, n, poly, outK, outD, sK, sD, offK, offD);
+    for (int base = 0; base < count;) {
+        const int np = count - base > 32 ? 2 : 1;
+        const float4 pc[2] = {pa[0], pa[1]};
+        const bool has[2] = {base + lane < count, np == 2 && base + 32 + lane < count};
+        const int nb = base + 32 * np;
+        if (nb < count) {
+            pa[0] = pts[min(nb + lane, count - 1)];
+            pa[1] = pts[min(nb + 32 + lane, count - 1)];
+        }
+        if (np == 2) gather_points<2, WK, WD>(t4, pc, has, n, poly, outK, outD, sK, sD, offK, offD);
+        else if (has[0]) gather_points<1, WK, WD>(t4, pc, has, n, poly, outK, outD, sK, sD, offK, offD);
+        base = nb;
+    }
 }
 
 // ----------------------------------------------------------------------------------
