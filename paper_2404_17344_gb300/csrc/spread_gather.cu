@@ -32,12 +32,13 @@ constexpr int kWarps = 8;                 // warps per block in the item kernels
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 // fast 3-D spread, m = 4 (W = 8)
-// Staged per point (STRIDE floats): xp[8] pairs (x_a v, x_a v) | wy[8] | zp[8] pairs (z_c, z_c).
-// The two half-warps take alternate staged points (hw = lane >> 4). Within a half-warp, lane
-// (ah, bh, cq) accumulates acc[a][p][i] = (g[4ah+a][4bh+2p][2cq+i], g[4ah+a][4bh+2p+1][2cq+i]): the
-// whole box per half-warp, 32 values per lane, so each point costs a lane 4 shared loads (16 bytes
-// each), 4 packed products and 16 packed FMAs, and a shared load serves twice as many FMAs as with
-// one box per warp. The two halves are summed once per item, before the atomic adds.
+// Staged per point (STRIDE floats): x_a v [8] | y [8] | z [8]. The two half-warps take alternate
+// staged points (hw = lane >> 4). Within a half-warp, lane (ah, bh, cq) accumulates
+// acc[a][p][i] = (g[4ah+a][4bh+2p][2cq+i], g[4ah+a][4bh+2p+1][2cq+i]): the whole box per half-warp,
+// 32 values per lane, so each point costs a lane 3 shared loads (16 + 16 + 8 bytes), 4 packed
+// products and 16 packed FMAs; the duplicated operands (x_a, x_a) and (z_c, z_c) the packed FMAs need
+// are formed in registers, which keeps the shared-memory traffic (the loop's tighter limit) at 40
+// bytes per lane and point. The two halves are summed once per item, before the atomic adds.
 //
 // Persistent: each warp takes work units (item, right-hand side) from a global counter, one unit
 // ahead, and loads the first batch of the next unit while it finishes the current one, so neither
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_spread3_w8(const int4* __res
                                                               const WinPoly poly)
 {
     constexpr int W = 8;
-    constexpr int STRIDE = 44;            // 16 + 8 + 16 floats, padded so staging stores avoid conflicts
+    constexpr int STRIDE = 28;            // 8 + 8 + 8 floats, padded so staging stores avoid conflicts
     __shared__ __align__(16) float sw[kWarps][32 * STRIDE];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* ws = sw[warp];
@@ -108,25 +109,24 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_spread3_w8(const int4* __res
             }
             if (lane < ncount) vn = __ldg((last ? v + (un / nitems) * ldv : vr) + __float_as_int(pn.w));
             float4* dst = reinterpret_cast<float4*>(ws + lane * STRIDE);
-#pragma unroll
-            for (int q = 0; q < W; q += 2) dst[q / 2] = make_float4(wx[q], wx[q], wx[q + 1], wx[q + 1]);
-            dst[4] = make_float4(wy[0], wy[1], wy[2], wy[3]);
-            dst[5] = make_float4(wy[4], wy[5], wy[6], wy[7]);
-#pragma unroll
-            for (int q = 0; q < W; q += 2) dst[6 + q / 2] = make_float4(wz[q], wz[q], wz[q + 1], wz[q + 1]);
+            dst[0] = make_float4(wx[0], wx[1], wx[2], wx[3]);
+            dst[1] = make_float4(wx[4], wx[5], wx[6], wx[7]);
+            dst[2] = make_float4(wy[0], wy[1], wy[2], wy[3]);
+            dst[3] = make_float4(wy[4], wy[5], wy[6], wy[7]);
+            dst[4] = make_float4(wz[0], wz[1], wz[2], wz[3]);
+            dst[5] = make_float4(wz[4], wz[5], wz[6], wz[7]);
             __syncwarp();
             // rows cnt .. 31 hold zeros (lanes without a point stage zero weights), so an odd count is safe
             const int cnt = min(32, count - base);
             const float* src = ws + hw * STRIDE;
 #pragma unroll 2
             for (int j = 0; j < cnt; j += 2, src += 2 * STRIDE) {
-                const float4 x01 = *reinterpret_cast<const float4*>(src + 8 * ah);        // a = 4ah, 4ah+1
-                const float4 x23 = *reinterpret_cast<const float4*>(src + 8 * ah + 4);    // a = 4ah+2, 4ah+3
-                const float4 yb = *reinterpret_cast<const float4*>(src + 16 + 4 * bh);    // b = 4bh .. 4bh+3
-                const float4 zz = *reinterpret_cast<const float4*>(src + 24 + 4 * cq);    // c = 2cq, 2cq+1 (pairs)
+                const float4 xa = *reinterpret_cast<const float4*>(src + 4 * ah);         // a = 4ah .. 4ah+3
+                const float4 yb = *reinterpret_cast<const float4*>(src + 8 + 4 * bh);     // b = 4bh .. 4bh+3
+                const float2 zc = *reinterpret_cast<const float2*>(src + 16 + 2 * cq);    // c = 2cq, 2cq+1
                 const float2 Y[2] = {f2(yb.x, yb.y), f2(yb.z, yb.w)};
-                const float2 Z[2] = {f2(zz.x, zz.y), f2(zz.z, zz.w)};
-                const float2 X[4] = {f2(x01.x, x01.y), f2(x01.z, x01.w), f2(x23.x, x23.y), f2(x23.z, x23.w)};
+                const float2 Z[2] = {f2(zc.x, zc.x), f2(zc.y, zc.y)};
+                const float2 X[4] = {f2(xa.x, xa.x), f2(xa.y, xa.y), f2(xa.z, xa.z), f2(xa.w, xa.w)};
                 float2 B[2][2];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) B[q >> 1][q & 1] = __fmul2_rn(Y[q >> 1], Z[q & 1]);
