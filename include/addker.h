@@ -84,6 +84,9 @@ typedef struct {
                             max(1, floor(M eps_B + 1/2)); 0 = no regularisation (plain periodic continuation) */
     int    window;       /* ADDKER_WIN_KB */
     int    kernel;       /* ADDKER_KERNEL_GAUSS (default) or ADDKER_KERNEL_MATERN12 */
+    int    compensated;  /* 1: compensated grid accumulation (each atomic add's rounding error, found by the
+                            error-free two-sum from the value the add returned, is accumulated in an error
+                            grid that the forward transform adds back); 0 (default): plain FP32 adds */
     void*  stream;       /* cudaStream_t for every product of this plan; NULL = legacy default stream */
 } addker_opts;
 

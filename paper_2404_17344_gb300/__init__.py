@@ -56,7 +56,7 @@ class AddKer:
     KERNELS = {"gauss": native.ADDKER_KERNEL_GAUSS, "matern": native.ADDKER_KERNEL_MATERN12}
 
     def __init__(self, points, windows, ell, sigma_f=1.0, bandwidth=32, cutoff=4, eps_B=1.0 / 16.0,
-                 p=-1, sigma_os=2.0, kernel="gauss"):
+                 p=-1, sigma_os=2.0, kernel="gauss", compensated=False):
         L = native.lib()
         pts = _dev_f32(points, "points")
         if pts.dim() != 2:
@@ -76,6 +76,7 @@ class AddKer:
         if kernel not in self.KERNELS:
             raise ValueError(f"kernel must be one of {sorted(self.KERNELS)}")
         opts.kernel = self.KERNELS[kernel]
+        opts.compensated = 1 if compensated else 0
         opts.stream = _stream_ptr()
         plan = ctypes.c_void_p()
         native.check(L.addker_setup(ctypes.byref(plan), ctypes.c_void_p(pts.data_ptr()), self.N, self.d, off, feat,

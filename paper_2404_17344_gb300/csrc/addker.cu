@@ -824,14 +824,20 @@ int ensure_slots(Plan& p, int want)
     for (int s = 0; s < p.P; ++s) {
         WinDev& w = p.win[s];
         float* grid;
+        float* gerr = nullptr;
         float2* hh;
         float4 *b1, *b2;
         CS(take(&grid, r * w.gsz));
+        if (p.comp) {
+            CS(take(&gerr, r * w.gsz));
+            CK(cudaMemsetAsync(gerr, 0, sizeof(float) * (size_t)(r * w.gsz), p.stream));
+        }
         CS(take(&hh, r * w.gsz));
         CS(take(&b1, r * w.b1sz));
         CS(take(&b2, r * w.b2sz));
         CK(cudaMemsetAsync(grid, 0, sizeof(float) * (size_t)(r * w.gsz), p.stream));
         w.grid = grid;
+        w.gerr = gerr;
         w.h = hh;
         w.buf1 = b1;
         w.buf2 = b2;
@@ -1077,6 +1083,7 @@ int addker_opts_default(addker_opts* o)
     o->p = -1;
     o->window = ADDKER_WIN_KB;
     o->kernel = ADDKER_KERNEL_GAUSS;
+    o->compensated = 0;
     o->stream = nullptr;
     return ADDKER_OK;
 }
@@ -1092,7 +1099,8 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
     if (N < 1 || N > 0x7fffffffLL || d < 1 || P < 1 || P > kMaxWindows || !win_off || !win_feat || !ell || !bandwidth)
         return ADDKER_EINVAL;
     if (!(sigma_f > 0.0) || cutoff < 2 || cutoff > 8 || o.window != ADDKER_WIN_KB ||
-        (o.kernel != ADDKER_KERNEL_GAUSS && o.kernel != ADDKER_KERNEL_MATERN12))
+        (o.kernel != ADDKER_KERNEL_GAUSS && o.kernel != ADDKER_KERNEL_MATERN12) ||
+        (o.compensated != 0 && o.compensated != 1))
         return ADDKER_EINVAL;
     if (!(o.eps_B > 0.0 && o.eps_B < 0.5) || !(o.sigma_os >= 1.25 && o.sigma_os <= 4.0) || o.p < -1 || o.p > 12)
         return ADDKER_EINVAL;
@@ -1125,6 +1133,7 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
     p.eps_B = o.eps_B;
     p.p_opt = o.p;
     p.kernel = o.kernel;
+    p.comp = o.compensated == 1;
     p.stream = static_cast<cudaStream_t>(o.stream);
     p.feat_off.assign(win_off, win_off + P + 1);
     p.feat.assign(win_feat, win_feat + win_off[P]);
@@ -1519,9 +1528,13 @@ int addker_debug_stage(addker_plan* plan, int window, int stage, const float* v,
     CK(cudaMemsetAsync(w.grid, 0, sizeof(float) * gsz, st));
     CK(launch_spread(p, window, v, p.N, 1, st));                     // slot 0
     if (stage == 0) {
-        std::vector<float> g(gsz);
+        std::vector<float> g(gsz), ge(w.gerr ? gsz : 0);
         CK(cudaMemcpyAsync(g.data(), w.grid, sizeof(float) * gsz, cudaMemcpyDeviceToHost, st));
         CK(cudaMemsetAsync(w.grid, 0, sizeof(float) * gsz, st));        // products expect a zeroed grid
+        if (w.gerr) {
+            CK(cudaMemcpyAsync(ge.data(), w.gerr, sizeof(float) * gsz, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemsetAsync(w.gerr, 0, sizeof(float) * gsz, st));
+        }
         CK(cudaStreamSynchronize(st));
         // the device window is w = phi * C with C = pi m / sinh(b m); report in phi's normalisation
         double b = M_PI * (2.0 - 1.0 / p.sigma_os);
@@ -1534,12 +1547,13 @@ int addker_debug_stage(addker_plan* plan, int window, int stage, const float* v,
             int64_t idx = a0;
             if (w.D >= 2) idx = idx * w.n + a1;
             if (w.D >= 3) idx = idx * w.n + a2;
-            out[idx] = g[i] * scale;
+            out[idx] = ((double)g[i] + (w.gerr ? (double)ge[i] : 0.0)) * scale;
         }
         return ADDKER_OK;
     }
     CK(launch_transforms(p, window, 1, st, nullptr, true));
     CK(cudaMemsetAsync(w.grid, 0, sizeof(float) * gsz, st));        // d = 3: the inverse pass that clears it did not run
+    if (w.gerr) CK(cudaMemsetAsync(w.gerr, 0, sizeof(float) * gsz, st));
     std::vector<float4> s(md);
     CK(cudaMemcpyAsync(s.data(), w.spec, sizeof(float4) * md, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

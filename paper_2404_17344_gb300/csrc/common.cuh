@@ -51,6 +51,7 @@ struct WinPoly {
 struct WinDev {                          // copied by value into kernel parameter space
     const float4* pts;
     float* grid;
+    float* gerr;                         // compensation grid (same layout as grid) or NULL
     float2* h;
     float4* buf1;
     float4* buf2;
@@ -77,6 +78,7 @@ struct Plan {
     double sigma_f = 1.0, sigma_os = 2.0, eps_B = 1.0 / 16.0;
     int p_opt = -1;
     int kernel = ADDKER_KERNEL_GAUSS;     // radial profile family (addker_opts.kernel)
+    bool comp = false;                    // compensated grid accumulation (addker_opts.compensated)
     cudaStream_t stream = nullptr;
     std::vector<int> dims, bandwidth, feat_off, feat;
     std::vector<double> ell;
@@ -180,6 +182,22 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // earlier kernel touches. The spread and gather kernels (thousands of blocks) are launched plainly:
 // the wait in every warp cost them more than the overlap saved.
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+// Add x to the grid value *g. With an error grid e (compensated accumulation), the rounding error of
+// the add goes to *e: the atomic returns the old value a and stores fl(a + x), so the error-free
+// two-sum (Knuth) of a and x recovers that error exactly; the forward transform adds e back to g.
+__device__ __forceinline__ void grid_add(float* g, float* e, float x)
+{
+    if (e == nullptr) {
+        atomicAdd(g, x);
+        return;
+    }
+    const float a = atomicAdd(g, x);
+    const float s = a + x;
+    const float bv = s - a;
+    const float err = (a - (s - bv)) + (x - bv);
+    atomicAdd(e, err);
+}
 
 // ---- device window weights ------------------------------------------------------------
 // The W = 2m weights of one coordinate x on a grid of n points; *cell = floor(n x) + n/2.

@@ -89,6 +89,10 @@ __global__ void __launch_bounds__(kT3) k_fwd_yz(const WinDev* __restrict__ wins,
     const float* g = W.grid + r * W.gsz + (size_t)x * b1 * b2;
     for (int i = threadIdx.x; i < b1 * b2; i += kT3) cp_async4(gs + i, g + i);
     cp_async_wait_all();
+    if (W.gerr) {                                              // compensated grid: add the error grid
+        const float* ge = W.gerr + r * W.gsz + (size_t)x * b1 * b2;
+        for (int i = threadIdx.x; i < b1 * b2; i += kT3) gs[i] += ge[i];
+    }
     __syncthreads();
     // phase 1: rows y (2 per thread, clamped), columns k (2 per thread)
     const int nb1 = (b1 + 1) / 2;
@@ -258,6 +262,10 @@ __global__ void __launch_bounds__(kT3) k_inv_yz(const WinDev* __restrict__ wins,
     float* g = W.grid + r * W.gsz + (size_t)x * b1 * b2 + (size_t)yb * b2;
     const int zrows = min(ny, b1 - yb);
     for (int i = threadIdx.x; i < zrows * b2; i += kT3) g[i] = 0.f;
+    if (W.gerr) {
+        float* ge = W.gerr + r * W.gsz + (size_t)x * b1 * b2 + (size_t)yb * b2;
+        for (int i = threadIdx.x; i < zrows * b2; i += kT3) ge[i] = 0.f;
+    }
     cp_async_wait_all();
     __syncthreads();
     const int Mh = M / 2;
@@ -365,6 +373,13 @@ __global__ void __launch_bounds__(kT) k_small_transform(const WinDev* __restrict
     for (int i = threadIdx.x; i < b0 * b1; i += kT) cp_async4(gs + i, grid + i);
     cp_async_wait_all();
     for (int i = threadIdx.x; i < b0 * b1; i += kT) grid[i] = 0.f;     // each thread clears what it copied
+    if (W.gerr) {                                              // compensated grid: add and clear the errors
+        float* ge = W.gerr + r * W.gsz;
+        for (int i = threadIdx.x; i < b0 * b1; i += kT) {
+            gs[i] += ge[i];
+            ge[i] = 0.f;
+        }
+    }
     __syncthreads();
     if (D == 1) {
         for (int k = threadIdx.x; k < M; k += kT) {

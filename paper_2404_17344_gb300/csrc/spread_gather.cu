@@ -153,14 +153,16 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_spread3_w8(const int4* __res
         const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff, cz = (it.z >> 16) & 0xff;
         const int ox = cx - 3 - P->lo[0], oy = cy - 3 - P->lo[1], oz = cz - 3 - P->lo[2];
         const int sy = P->box[2], sx = P->box[1] * P->box[2];
-        float* g = P->grid + r * P->gsz + (size_t)(ox + 4 * ah) * sx + (size_t)(oy + 4 * bh) * sy + oz + 2 * cq + hw;
+        const size_t o0 = r * P->gsz + (size_t)(ox + 4 * ah) * sx + (size_t)(oy + 4 * bh) * sy + oz + 2 * cq + hw;
+        float* g = P->grid + o0;
+        float* ge = P->gerr ? P->gerr + o0 : nullptr;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            float* ga = g + (size_t)a * sx;
-            atomicAdd(ga, acc[a][0][0].x);
-            atomicAdd(ga + sy, acc[a][0][0].y);
-            atomicAdd(ga + 2 * sy, acc[a][1][0].x);
-            atomicAdd(ga + 3 * sy, acc[a][1][0].y);
+            const size_t oa = (size_t)a * sx;
+            grid_add(g + oa, ge ? ge + oa : nullptr, acc[a][0][0].x);
+            grid_add(g + oa + sy, ge ? ge + oa + sy : nullptr, acc[a][0][0].y);
+            grid_add(g + oa + 2 * sy, ge ? ge + oa + 2 * sy : nullptr, acc[a][1][0].x);
+            grid_add(g + oa + 3 * sy, ge ? ge + oa + 3 * sy : nullptr, acc[a][1][0].y);
         }
         if (!more) break;
         // advance: the prefetched unit becomes current; take the one after it
@@ -410,7 +412,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_spread_lowd_w8(const int4* __re
         for (int e = 0; e < (NV >= 32 ? NV / 32 : 1); ++e) {
             const int idx = base + e;
             const int a = D == 1 ? idx : idx / W, b = D == 1 ? 0 : idx % W;
-            atomicAdd(P.grid + r * P.gsz + (size_t)(ox + a) * P.box[1] + (D >= 2 ? oy + b : 0), acc[e]);
+            const size_t o = r * P.gsz + (size_t)(ox + a) * P.box[1] + (D >= 2 ? oy + b : 0);
+            grid_add(P.grid + o, P.gerr ? P.gerr + o : nullptr, acc[e]);
         }
     }
 }
@@ -533,7 +536,7 @@ __global__ void __launch_bounds__(128) k_spread_generic(const int4* __restrict__
         if (D == 2) { a = i / W; bb = i % W; }
         if (D == 3) { a = i / (W * W); bb = (i / W) % W; cc = i % W; }
         const size_t g = ((size_t)(ox + a) * P.box[1] + (D >= 2 ? oy + bb : 0)) * P.box[2] + (D >= 3 ? oz + cc : 0);
-        if (box[i] != 0.f) atomicAdd(P.grid + r * P.gsz + g, box[i]);
+        if (box[i] != 0.f) grid_add(P.grid + r * P.gsz + g, P.gerr ? P.gerr + r * P.gsz + g : nullptr, box[i]);
     }
 }
 

@@ -31,7 +31,8 @@ def ADDKER_ELL(s: int) -> int:
 
 class addker_opts(ctypes.Structure):
     _fields_ = [("sigma_os", ctypes.c_double), ("eps_B", ctypes.c_double), ("p", ctypes.c_int),
-                ("window", ctypes.c_int), ("kernel", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("window", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("compensated", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 # name -> (restype, argtypes); every entry point of include/addker.h

@@ -58,6 +58,7 @@ def test_strerror_and_defaults(lib):
     o = native.addker_opts()
     assert lib.addker_opts_default(ctypes.byref(o)) == 0
     assert o.sigma_os == 2.0 and o.eps_B == 1 / 16 and o.p == -1 and o.kernel == native.ADDKER_KERNEL_GAUSS
+    assert o.compensated == 0 and ctypes.sizeof(o) == 40
     assert lib.addker_opts_default(None) == native.ADDKER_EINVAL
     assert lib.addker_free(None) == 0
 
