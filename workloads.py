@@ -63,20 +63,20 @@ class Workload:
             return rng.standard_normal(self.N).astype(np.float32)
         return rng.standard_normal((nrhs, self.N)).astype(np.float32).T.copy()
 
-    def targets(self, features: int = 64, noise: float = 0.1) -> np.ndarray:
-        """Regression targets for the GP/KRR loop: a random-Fourier-feature function of the points,
-        y = sqrt(2/F) sum_f a_f cos(omega_f . x + b_f) + noise * eps, with omega_f ~ N(0, 1/ell0^2) in
-        every window's coordinates (ell0 = the median length scale), a_f, eps ~ N(0, 1),
-        b_f ~ U[0, 2 pi). Seed + 3. Shape (N,), float32."""
+    def targets(self, terms: int = 16, noise_var: float = 0.01) -> np.ndarray:
+        """Regression targets for the GP/KRR loop: a sum over the windows of random smooth functions of
+        the window's features, each a random-Fourier-feature expansion with `terms` terms,
+        f_s(x) = sqrt(2/F) sum_f a_f cos(omega_f . x^W_s + b_f), omega_f ~ N(0, I/ell_s^2),
+        a_f ~ N(0, 1), b_f ~ U[0, 2 pi), plus N(0, noise_var) noise. Seed + 3. Shape (N,), float32."""
         rng = np.random.Generator(np.random.PCG64(self.seed + 3))
-        feats = sorted({f for w in self.windows for f in w})
-        ell0 = float(np.median(self.ell))
-        X = self.points[:, feats].astype(np.float64)
-        omega = rng.standard_normal((features, len(feats))) / ell0
-        a = rng.standard_normal(features)
-        b = rng.uniform(0.0, 2.0 * np.pi, size=features)
-        y = np.sqrt(2.0 / features) * (np.cos(X @ omega.T + b) @ a)
-        y += noise * rng.standard_normal(self.N)
+        y = np.zeros(self.N)
+        for s, w in enumerate(self.windows):
+            X = self.points[:, list(w)].astype(np.float64)
+            omega = rng.standard_normal((terms, len(w))) / float(self.ell[s])
+            a = rng.standard_normal(terms)
+            b = rng.uniform(0.0, 2.0 * np.pi, size=terms)
+            y += np.sqrt(2.0 / terms) * (np.cos(X @ omega.T + b) @ a)
+        y += np.sqrt(noise_var) * rng.standard_normal(self.N)
         return y.astype(np.float32)
 
     def probes(self, m: int) -> np.ndarray:
