@@ -71,6 +71,10 @@ void release(Plan& p)
     clear_graphs(p);
     if (p.cap_stream) cudaStreamDestroy(p.cap_stream);
     p.cap_stream = nullptr;
+    if (p.copy_stream) cudaStreamDestroy(p.copy_stream);
+    p.copy_stream = nullptr;
+    for (cudaEvent_t e : p.win_events) cudaEventDestroy(e);
+    p.win_events.clear();
     if (p.items) cudaFree(p.items);
     p.items = nullptr;
     p.items_cap = 0;
@@ -1389,6 +1393,37 @@ int addker_matvec_all_host(addker_plan* plan, const float* v, float* Kv, float* 
         k_copy<<<cb, 256, 0, st>>>(src, dst, n, vec);
         return cudaGetLastError();
     };
+    if (nrhs == 1 && dKdell && p.P > 1) {
+        // one right-hand side: the windows are gathered one launch each, and each window's derivative
+        // product is copied to the host on a second stream while the next window is gathered; only K v
+        // (after the window sum) and the last window's copy remain after the last gather
+        if (!p.copy_stream) CK(cudaStreamCreateWithFlags(&p.copy_stream, cudaStreamNonBlocking));
+        while ((int)p.win_events.size() < p.P) {
+            cudaEvent_t e;
+            CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            p.win_events.push_back(e);
+        }
+        CS(ensure_slots(p, 1));
+        const int64_t N = p.N;
+        CK(cudaMemcpyAsync(p.stage_v, v, sizeof(float) * N, cudaMemcpyHostToDevice, st));
+        CK(launch_spread(p, -1, p.stage_v, N, 1, st));
+        CK(launch_transforms(p, -1, 1, st, nullptr, false));
+        const float* ones = p.scale_dev;
+        const float* sder = p.scale_dev + 2 * p.P;
+        for (int s = 0; s < p.P; ++s) {
+            CK(launch_gather(p, s, p.ks, N, 0, p.stage_d, N, 0, 1, ones, sder, st));
+            CK(cudaEventRecord(p.win_events[s], st));
+            CK(cudaStreamWaitEvent(p.copy_stream, p.win_events[s], 0));
+            CK(cudaMemcpyAsync(dKdell + s * N, p.stage_d + s * N, sizeof(float) * N, cudaMemcpyDeviceToHost,
+                               p.copy_stream));
+        }
+        window_sum(p, 1, (float)(p.sigma_f * p.sigma_f), p.stage_k, N, st);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(Kv, p.stage_k, sizeof(float) * N, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(p.copy_stream));
+        CK(cudaStreamSynchronize(st));
+        return ADDKER_OK;
+    }
     const float* vm = static_cast<const float*>(mapped(v));
     float* Km = static_cast<float*>(mapped(Kv));
     float* Dm = dKdell ? static_cast<float*>(mapped(dKdell)) : nullptr;

@@ -128,6 +128,8 @@ struct Plan {
     std::vector<std::pair<GraphKey, cudaGraphExec_t>> graph_cache;   // most recent last
     GraphKey last_key = {nullptr, nullptr, nullptr, 0, 0, -1};
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;   // device-to-host copies overlapped with later gathers (host entry)
+    std::vector<cudaEvent_t> win_events;  // one per window: its gather has finished
     int64_t graph_replays = 0;
 };
 
