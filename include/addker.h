@@ -18,7 +18,20 @@
  * FFT, multiplication by the Fourier coefficients of the regularised kernel
  * (Lemma "aliasing error": coefficients from M^{d_s} samples), inverse FFT,
  * interpolation (NFFT). Every step of a product runs in CUDA kernels on the
- * device; FP32 arithmetic, FP64 only in the coefficient precomputation.
+ * device; FP32 arithmetic, FP64 only in the coefficient precomputation and in
+ * the inner products of the solvers.
+ *
+ * Entry points:
+ *   plan         addker_opts_default, addker_setup, addker_set_params, addker_set_stream,
+ *                addker_set_graphs, addker_autotune, addker_free, addker_info
+ *   products     addker_matvec, addker_dmatvec, addker_matvec_all (device buffers),
+ *                addker_matvec_all_host (host buffers), addker_fastsum_noalloc (no plan)
+ *   gradients    addker_vjp (w^T K v with respect to v, ell, sigma_f and the points)
+ *   solvers      addker_cg (regression system, Sec. 3.3), addker_gp_grad (GP training)
+ *   analysis     addker_gsi (global sensitivity indices, Sec. 4)
+ *   utilities    addker_prescale, addker_sync, addker_strerror, addker_profile,
+ *                addker_profile_read, addker_debug_stage
+ * The additive Matern(1/2) kernel of Sec. 5 is selected by addker_opts.kernel.
  *
  * Conventions for every call:
  *   - Return 0 on success or a negative ADDKER_E* code; addker_strerror() names it.
