@@ -247,26 +247,30 @@ __device__ __forceinline__ void gather_points(const float4* t4, const float4 (&p
 // staged in shared memory as float2 (h^K, h^D) and read back as float4 (two such pairs). The pair
 // (h^K, h^D) is contracted with duplicated weights in one packed FMA, so each 16-byte broadcast load
 // feeds 4 packed FMAs (8 FMAs) for the lane's two points.
+// The gather arguments every item routine takes: outputs (window s and right-hand side r of point i
+// at out[i + s*stride + r*rstride]), per-window scales, and the window polynomials.
+struct GatherArgs {
+    float* outK;
+    float* outD;
+    const float* scaleK;
+    const float* scaleD;
+    int64_t strideK, strideD, rstrideK, rstrideD;
+};
+
+// One 3-D item (m = 4) by one warp; t is the warp's 512-entry tile.
 template <bool WK, bool WD>
-__global__ void __launch_bounds__(kWarps * 32, 2) k_gather3_w8(const int4* __restrict__ items, int nitems,
-                                                              const WinDev* __restrict__ wins,
-                                                              float* __restrict__ outK, float* __restrict__ outD,
-                                                              const float* __restrict__ scaleK,
-                                                              const float* __restrict__ scaleD, int64_t strideK,
-                                                              int64_t strideD, int64_t rstrideK, int64_t rstrideD,
-                                                              const WinPoly poly)
+__device__ __forceinline__ void gather3_item(const int4 it, const WinDev& P, float2* t, int lane, int r,
+                                             const GatherArgs& g, const WinPoly& poly)
 {
     constexpr int W = 8;
-    __shared__ __align__(16) float2 tile[kWarps][W * W * W];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int item = blockIdx.x * kWarps + warp;
-    if (item >= nitems) return;
-    const int4 it = items[item];
-    const WinDev& P = wins[it.w];
+    float* __restrict__ outK = g.outK;
+    float* __restrict__ outD = g.outD;
+    const int64_t strideK = g.strideK, strideD = g.strideD, rstrideK = g.rstrideK, rstrideD = g.rstrideD;
+    const float* __restrict__ scaleK = g.scaleK;
+    const float* __restrict__ scaleD = g.scaleD;
     const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff, cz = (it.z >> 16) & 0xff;
     const int ox = cx - 3 - P.lo[0], oy = cy - 3 - P.lo[1], oz = cz - 3 - P.lo[2];
     const int sy = P.box[2], sx = P.box[1] * P.box[2];
-    const int r = blockIdx.y;                                  // right-hand side
     const float2* __restrict__ h = P.h + r * P.gsz + (size_t)ox * sx + (size_t)oy * sy + oz;
     const float4* __restrict__ pts = P.pts + it.x;
     const int count = it.y;
@@ -274,7 +278,6 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_gather3_w8(const int4* __res
     float4 pa[2];
     pa[0] = pts[min(lane, count - 1)];
     pa[1] = pts[min(lane + 32, count - 1)];
-    float2* t = tile[warp];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         const int idx = lane + 32 * i;
@@ -301,6 +304,19 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_gather3_w8(const int4* __res
         else if (has[0]) gather_points<1, WK, WD>(t4, pc, has, n, poly, outK, outD, sK, sD, offK, offD);
         base = nb;
     }
+}
+
+template <bool WK, bool WD>
+__global__ void __launch_bounds__(kWarps * 32, 2) k_gather3_w8(const int4* __restrict__ items, int nitems,
+                                                              const WinDev* __restrict__ wins, GatherArgs g,
+                                                              const WinPoly poly)
+{
+    __shared__ __align__(16) float2 tile[kWarps][512];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * kWarps + warp;
+    if (item >= nitems) return;
+    const int4 it = items[item];
+    gather3_item<WK, WD>(it, wins[it.w], tile[warp], lane, blockIdx.y, g, poly);
 }
 
 // ----------------------------------------------------------------------------------
@@ -418,27 +434,20 @@ __global__ void __launch_bounds__(kWarps * 32) k_spread_lowd_w8(const int4* __re
     }
 }
 
+// One 1-D or 2-D item (m = 4) by one warp; t holds at least (2m)^D entries.
 template <int D, bool WK, bool WD>
-__global__ void __launch_bounds__(kWarps * 32) k_gather_lowd_w8(const int4* __restrict__ items, int nitems,
-                                                               const WinDev* __restrict__ wins,
-                                                               float* __restrict__ outK, float* __restrict__ outD,
-                                                               const float* __restrict__ scaleK,
-                                                               const float* __restrict__ scaleD, int64_t strideK,
-                                                               int64_t strideD, int64_t rstrideK, int64_t rstrideD,
-                                                               const WinPoly poly)
+__device__ __forceinline__ void gather_lowd_item(const int4 it, const WinDev& P, float2* t, int lane, int r,
+                                                 const GatherArgs& g, const WinPoly& poly)
 {
     constexpr int W = 8;
     constexpr int NV = D == 1 ? W : W * W;
-    __shared__ __align__(16) float2 tile[kWarps][NV];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int item = blockIdx.x * kWarps + warp;
-    if (item >= nitems) return;
-    const int4 it = items[item];
-    const WinDev& P = wins[it.w];
+    float* __restrict__ outK = g.outK;
+    float* __restrict__ outD = g.outD;
+    const int64_t strideK = g.strideK, strideD = g.strideD, rstrideK = g.rstrideK, rstrideD = g.rstrideD;
+    const float* __restrict__ scaleK = g.scaleK;
+    const float* __restrict__ scaleD = g.scaleD;
     const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff;
     const int ox = cx - 3 - P.lo[0], oy = cy - 3 - P.lo[1];
-    float2* t = tile[warp];
-    const int r = blockIdx.y;                                  // right-hand side
     const float2* __restrict__ h = P.h + r * P.gsz;
     for (int i = lane; i < NV; i += 32) {
         const int a = D == 1 ? i : i / W, b = D == 1 ? 0 : i % W;
@@ -488,6 +497,37 @@ __global__ void __launch_bounds__(kWarps * 32) k_gather_lowd_w8(const int4* __re
             if (WD) outD[i + it.w * strideD + r * rstrideD] = sD * f.y;
         }
     }
+}
+
+template <int D, bool WK, bool WD>
+__global__ void __launch_bounds__(kWarps * 32) k_gather_lowd_w8(const int4* __restrict__ items, int nitems,
+                                                               const WinDev* __restrict__ wins, GatherArgs g,
+                                                               const WinPoly poly)
+{
+    __shared__ __align__(16) float2 tile[kWarps][D == 1 ? 8 : 64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * kWarps + warp;
+    if (item >= nitems) return;
+    const int4 it = items[item];
+    gather_lowd_item<D, WK, WD>(it, wins[it.w], tile[warp], lane, blockIdx.y, g, poly);
+}
+
+// Every m = 4 item of every window in one launch (items of the 3-D, 1-D and 2-D kinds are contiguous):
+// each warp takes the routine of its item's dimension, so mixed windows share one grid and one tail.
+template <bool WK, bool WD>
+__global__ void __launch_bounds__(kWarps * 32, 2) k_gather_w8_all(const int4* __restrict__ items, int nitems,
+                                                                 const WinDev* __restrict__ wins, GatherArgs g,
+                                                                 const WinPoly poly)
+{
+    __shared__ __align__(16) float2 tile[kWarps][512];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * kWarps + warp;
+    if (item >= nitems) return;
+    const int4 it = items[item];
+    const WinDev& P = wins[it.w];
+    if (P.D == 3) gather3_item<WK, WD>(it, P, tile[warp], lane, blockIdx.y, g, poly);
+    else if (P.D == 2) gather_lowd_item<2, WK, WD>(it, P, tile[warp], lane, blockIdx.y, g, poly);
+    else gather_lowd_item<1, WK, WD>(it, P, tile[warp], lane, blockIdx.y, g, poly);
 }
 
 // ----------------------------------------------------------------------------------
@@ -662,37 +702,41 @@ static int gather_all(const Plan& p, int window, float* oK, int64_t zK, int64_t 
 {
     int launched = 0;
     const WinDev* wd = p.wins_dev;
-    for (int k = 0; k < kKinds; ++k) {
+    const GatherArgs g = {oK, oD, sK, sD, zK, zD, rK, rD};
+    const dim3 T(kWarps * 32), T2(128);
+    int k0 = 0;
+    if (window < 0) {
+        // the m = 4 kinds (3-D, 1-D, 2-D fast) lie next to each other: one launch for all of them
+        const int lo = p.item_begin[kKindFast3].front(), hi = p.item_begin[kKindLow2].back();
+        if (hi > lo) {
+            const int n = hi - lo;
+            launch_k(false, k_gather_w8_all<WK, WD>, dim3((n + kWarps - 1) / kWarps, nrhs), T, 0, st, p.items + lo, n,
+                     wd, g, p.poly);
+            ++launched;
+        }
+        k0 = kKindGen1;
+    }
+    for (int k = k0; k < kKinds; ++k) {
         int lo, hi;
         item_range(p, k, window, &lo, &hi);
         if (hi <= lo) continue;
         const int n = hi - lo;
         const int4* it = p.items + lo;
         const dim3 warps((n + kWarps - 1) / kWarps, nrhs), blocks(n, nrhs);
-        const bool pdl = false;                // griddepcontrol.wait in every warp measured slower
-        const dim3 T(kWarps * 32), T2(128);
         switch (k) {
-            case kKindFast3:
-                launch_k(pdl, k_gather3_w8<WK, WD>, warps, T, 0, st, it, n, wd, oK, oD, sK, sD, zK, zD, rK, rD, p.poly);
-                break;
-            case kKindLow1:
-                launch_k(pdl, k_gather_lowd_w8<1, WK, WD>, warps, T, 0, st, it, n, wd, oK, oD, sK, sD, zK, zD, rK, rD,
-                         p.poly);
-                break;
-            case kKindLow2:
-                launch_k(pdl, k_gather_lowd_w8<2, WK, WD>, warps, T, 0, st, it, n, wd, oK, oD, sK, sD, zK, zD, rK, rD,
-                         p.poly);
-                break;
+            case kKindFast3: launch_k(false, k_gather3_w8<WK, WD>, warps, T, 0, st, it, n, wd, g, p.poly); break;
+            case kKindLow1: launch_k(false, k_gather_lowd_w8<1, WK, WD>, warps, T, 0, st, it, n, wd, g, p.poly); break;
+            case kKindLow2: launch_k(false, k_gather_lowd_w8<2, WK, WD>, warps, T, 0, st, it, n, wd, g, p.poly); break;
             case kKindGen1:
-                launch_k(pdl, k_gather_generic<1, WK, WD>, blocks, T2, 0, st, it, wd, oK, oD, sK, sD, zK, zD, rK, rD,
+                launch_k(false, k_gather_generic<1, WK, WD>, blocks, T2, 0, st, it, wd, oK, oD, sK, sD, zK, zD, rK, rD,
                          p.poly);
                 break;
             case kKindGen2:
-                launch_k(pdl, k_gather_generic<2, WK, WD>, blocks, T2, 0, st, it, wd, oK, oD, sK, sD, zK, zD, rK, rD,
+                launch_k(false, k_gather_generic<2, WK, WD>, blocks, T2, 0, st, it, wd, oK, oD, sK, sD, zK, zD, rK, rD,
                          p.poly);
                 break;
             default:
-                launch_k(pdl, k_gather_generic<3, WK, WD>, blocks, T2, 0, st, it, wd, oK, oD, sK, sD, zK, zD, rK, rD,
+                launch_k(false, k_gather_generic<3, WK, WD>, blocks, T2, 0, st, it, wd, oK, oD, sK, sD, zK, zD, rK, rD,
                          p.poly);
                 break;
         }
