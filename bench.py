@@ -269,6 +269,10 @@ def run_ours(args, rank, world, local_rank):
     hbm_bytes = N * (2 * 4 * wl.d + 4 + 4 * (1 + P))
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
 
+    # measured FP32 and atomic rates of this device (after the timed region)
+    from paper_2404_17344_gb300 import device_rates
+    rates = device_rates()
+
     # CPU oracle baseline, bounded sample
     sample = min(N, args.cpu_sample)
     cpu_sec = cpu_oracle_step(wl, v_np, sample) * (N / sample)
@@ -300,7 +304,11 @@ def run_ours(args, rank, world, local_rank):
                         "timing": "CUDA events around the kernel's stage on the plan's stream, over K steps run "
                                   "right after the timed region (same inputs, L2 flushed between steps)",
                         "peak_source": f"FP32 FMA pipe: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz "
-                                       f"(sm_max_mhz {pk_kind})"},
+                                       f"(sm_max_mhz {pk_kind})",
+                        "peak_measured": rates["ffma2_tflops"],
+                        "frac_of_measured": achieved / rates["ffma2_tflops"] if rates["ffma2_tflops"] > 0 else None,
+                        "peak_measured_source": "packed FFMA2 microbenchmark (addker_device_rates) at "
+                                                f"{rates['sm_mhz_under_load']:.0f} MHz, after the timed region"},
            "roofline_hbm": {"achieved": hbm_bytes / (ms_per_step / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                             "frac": hbm_bytes / (ms_per_step / 1e3) / 1e9 / hbm_peak,
                             "note": f"algorithmic bytes of the whole step, {pk_kind} copy bandwidth"},
@@ -312,6 +320,7 @@ def run_ours(args, rank, world, local_rank):
                    "d2h_bytes_per_step": 4 * N * (1 + P)},
            "gpu_launches": launches * 1,
            "gpu_launches_per_step": launches / args.steps,
+           "device_rates": rates,
            "clocks": clk.summary(), "setup_ms": setup_ms, "wall_s_timed": wall,
            "accuracy": acc}
     print(json.dumps(out), flush=True)
@@ -449,6 +458,32 @@ def run_gp(args, rank, world, local_rank):
     op.close()
 
 
+def run_cpu_times(args, rank):
+    """CPU context for the headline workload (no GPU): one full-N FP64 oracle product on the host
+    cores (the oracle's OpenMP threads; OMP_NUM_THREADS=1 gives the one-core figure) and, with
+    --check-rows R, the direct FP64 sums on R random rows. Prints one JSON line."""
+    if rank != 0:
+        return
+    import numpy as np
+    import workloads
+    import oracle
+    wl = workloads.make("c1", N=args.N)
+    v = wl.vector().astype(np.float64)
+    sample = min(args.N, 20_000)
+    oracle.fastsum.matvec_all(wl.points[:sample], wl.windows, wl.ell, wl.sigma_f, v[:sample], wl.bandwidth,
+                              wl.cutoff)                                  # builds and warms the oracle library
+    t0 = time.perf_counter()
+    oracle.fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f, v, wl.bandwidth, wl.cutoff)
+    nfft_s = time.perf_counter() - t0
+    rows = np.random.default_rng(0).choice(wl.N, args.check_rows, replace=False)
+    t0 = time.perf_counter()
+    oracle.fastsum.direct(wl.points, wl.windows, wl.ell, wl.sigma_f, v, rows=rows)
+    direct_s = time.perf_counter() - t0
+    print(json.dumps({"mode": "cpu", "threads": cpu_cores(), "N": args.N,
+                      "oracle_nfft_units_per_s": 1.0 / nfft_s, "oracle_nfft_s_per_unit": nfft_s,
+                      "direct_rows": int(args.check_rows), "direct_s": direct_s}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -460,9 +495,10 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=100_000)
     ap.add_argument("--check-rows", type=int, default=256)
     ap.add_argument("--no-check", action="store_true")
-    ap.add_argument("--mode", default="product", choices=["product", "batched", "gp"],
+    ap.add_argument("--mode", default="product", choices=["product", "batched", "gp", "cpu"],
                     help="product: the headline fused product; batched: 7 mixed windows x 64 right-hand sides; "
-                         "gp: one GP gradient (CG + Hutchinson) per step")
+                         "gp: one GP gradient (CG + Hutchinson) per step; cpu: FP64 oracle timings on the host "
+                         "cores (no GPU)")
     ap.add_argument("--nrhs", type=int, default=64, help="right-hand sides per step (batched), 1 + probes (gp)")
     ap.add_argument("--beta", type=float, default=1.0,
                     help="gp: regularisation beta; the configuration's noise variance 0.01 leaves unpreconditioned "
@@ -479,6 +515,8 @@ def main():
         run_reference(args, rank, world)
     elif args.mode == "batched":
         run_batched(args, rank, world, local_rank)
+    elif args.mode == "cpu":
+        run_cpu_times(args, rank)
     elif args.mode == "gp":
         if args.nrhs == 64:
             args.nrhs = 17                       # y and 16 probes

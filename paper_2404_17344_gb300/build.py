@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libaddker.so")
-SOURCES = ["addker.cu", "fft.cu", "spread_gather.cu", "noalloc.cu", "gradients.cu", "solver.cu", "gsi.cu"]
+SOURCES = ["addker.cu", "fft.cu", "spread_gather.cu", "noalloc.cu", "gradients.cu", "solver.cu", "gsi.cu", "rates.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", 
          "-Xptxas", "-v"]

@@ -198,3 +198,16 @@ def test_autotune_keeps_results(torch_cuda, cfg, N, nrhs):
     for _ in range(3):
         K1, D1 = op.matvec_all(V)
     assert rel(K1.cpu(), K0.cpu()) < TOL and rel(D1.cpu(), D0.cpu()) < TOL
+
+
+def test_device_rates_are_plausible(torch_cuda):
+    """addker_device_rates: every rate positive; the FP32 rates within the FMA pipe's bound
+    (128 lanes per SM, 2 flops per FMA, at the measured clock; twice that for a packed
+    FMA issued at full rate) up to timer noise."""
+    from paper_2404_17344_gb300 import device_rates
+    r = device_rates()
+    assert r["sms"] > 0 and r["sm_mhz_under_load"] > 100
+    bound = r["sms"] * 128 * 2 * r["sm_mhz_under_load"] * 1e6 / 1e12
+    for k in ("ffma_tflops", "ffma2_tflops"):
+        assert 0.2 * bound < r[k] < 2.2 * bound, (k, r[k], bound)
+    assert r["shared_atomic_gops"] > 0 and r["global_atomic_gops"] > 0
