@@ -37,9 +37,9 @@ def lib():
             P = ctypes.c_void_p
             L.orc_direct.argtypes = [i64, i32, P, i32, P, P, P, f64, P, i64, P, P, P]
             L.orc_direct.restype = None
-            L.orc_spread.argtypes = [i64, i32, P, P, i32, i32, f64, P]
+            L.orc_spread.argtypes = [i64, i32, P, P, i32, i32, f64, i32, P]
             L.orc_spread.restype = None
-            L.orc_gather.argtypes = [i64, i32, P, i32, i32, f64, i32, P, P]
+            L.orc_gather.argtypes = [i64, i32, P, i32, i32, f64, i32, i32, P, P]
             L.orc_gather.restype = None
             L.orc_direct_grad_x.argtypes = [i64, i32, P, i32, P, P, P, f64, P, P, i64, P, P]
             L.orc_direct_grad_x.restype = None

@@ -107,34 +107,35 @@ def ndft_fastsum(x: np.ndarray, v: np.ndarray, chats) -> list:
     return [forward_exact(x, c * S).real for c in chats]
 
 
-def _phihat_grid(M: int, n: int, m: int, sigma: float, d: int) -> np.ndarray:
-    ph = window.phihat_quadrature(np.arange(-M // 2, M // 2), n, m, sigma)
+def _phihat_grid(M: int, n: int, m: int, sigma: float, d: int, win: str = "kb") -> np.ndarray:
+    ph = window.phihat_quadrature(np.arange(-M // 2, M // 2), n, m, sigma, window=win)
     out = ph
     for _ in range(d - 1):
         out = np.multiply.outer(out, ph)
     return out
 
 
-def nfft_adjoint(x: np.ndarray, v: np.ndarray, M: int, n: int, m: int, sigma: float = 2.0):
+def nfft_adjoint(x: np.ndarray, v: np.ndarray, M: int, n: int, m: int, sigma: float = 2.0, win: str = "kb"):
     """Approximate S_k, k in I_M^d: spread, n^d FFT, keep I_M, divide by n^d prod phi_hat."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     N, d = x.shape
     v = np.ascontiguousarray(v, dtype=np.float64)
     g = np.zeros((n,) * d)
-    _clib.lib().orc_spread(N, d, _clib.ptr(x), _clib.ptr(v), n, m, window.shape(sigma), _clib.ptr(g))
+    _clib.lib().orc_spread(N, d, _clib.ptr(x), _clib.ptr(v), n, m, window.shape_of(m, sigma, win),
+                           window.KINDS[win], _clib.ptr(g))
     G = np.fft.fftshift(np.fft.fftn(np.fft.ifftshift(g)))          # index k + n/2, k in I_n
     sl = tuple([slice(n // 2 - M // 2, n // 2 + M // 2)] * d)
-    return G[sl] / (n ** d * _phihat_grid(M, n, m, sigma, d))
+    return G[sl] / (n ** d * _phihat_grid(M, n, m, sigma, d, win))
 
 
-def nfft_forward(x: np.ndarray, dhats, n: int, m: int, sigma: float = 2.0) -> np.ndarray:
+def nfft_forward(x: np.ndarray, dhats, n: int, m: int, sigma: float = 2.0, win: str = "kb") -> np.ndarray:
     """Approximate f_q(x_i) = sum_k dhat_q,k exp(2 pi i k.x_i) for each dhat_q (real part kept):
     divide by n^d prod phi_hat, zero-pad to I_n, inverse n^d FFT, interpolate."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     N, d = x.shape
     M = dhats[0].shape[0]
     sl = tuple([slice(n // 2 - M // 2, n // 2 + M // 2)] * d)
-    phg = _phihat_grid(M, n, m, sigma, d)
+    phg = _phihat_grid(M, n, m, sigma, d, win)
     hs = []
     for dh in dhats:
         ghat = np.zeros((n,) * d, dtype=np.complex128)
@@ -143,18 +144,18 @@ def nfft_forward(x: np.ndarray, dhats, n: int, m: int, sigma: float = 2.0) -> np
         hs.append(h.real)
     H = np.ascontiguousarray(np.stack(hs))
     out = np.zeros((len(dhats), N))
-    _clib.lib().orc_gather(N, d, _clib.ptr(x), n, m, window.shape(sigma), len(dhats), _clib.ptr(H),
-                           _clib.ptr(out))
+    _clib.lib().orc_gather(N, d, _clib.ptr(x), n, m, window.shape_of(m, sigma, win), window.KINDS[win],
+                           len(dhats), _clib.ptr(H), _clib.ptr(out))
     return out
 
 
 def nfft_fastsum(x: np.ndarray, v: np.ndarray, chats, n: int, m: int, sigma: float = 2.0,
-                 targets: np.ndarray | None = None) -> np.ndarray:
+                 targets: np.ndarray | None = None, win: str = "kb") -> np.ndarray:
     """Level 3: adjoint NFFT -> multiply by c_hat -> NFFT, for each c_hat in chats (rows of the result).
     The sums are evaluated at `targets` (the x'_i of eq. "fast sum"), by default at the sources x."""
     M = chats[0].shape[0]
-    S = nfft_adjoint(x, v, M, n, m, sigma)
-    return nfft_forward(x if targets is None else targets, [c * S for c in chats], n, m, sigma)
+    S = nfft_adjoint(x, v, M, n, m, sigma, win)
+    return nfft_forward(x if targets is None else targets, [c * S for c in chats], n, m, sigma, win)
 
 
 KINDS = {"gauss": ("gauss", "der", 2.0), "matern": ("matern", "matern_der", 1.0)}
@@ -189,10 +190,11 @@ def direct_matern(points, windows, ell, sigma_f: float, v, rows=None, block: int
 
 def matvec_all(points, windows, ell, sigma_f: float, v, bandwidth, cutoff: int, p=None,
                eps_B: float = 1.0 / 16.0, sigma: float = 2.0, level: str = "nfft", rows=None,
-               kernel: str = "gauss"):
+               kernel: str = "gauss", win: str = "kb"):
     """Fused product: returns (K v, dK/d ell [P, .]) at level 'nfft' (CPU NFFT fast sum)
     or 'ndft' (exact trigonometric sum). v is one right-hand side of length N. With `rows`, the
-    outputs are evaluated only at those points (all N points are still sources)."""
+    outputs are evaluated only at those points (all N points are still sources). `win` selects the
+    NFFT window ('kb' Kaiser-Bessel, 'es' exponential of semicircle)."""
     X = np.asarray(points, dtype=np.float32).astype(np.float64)
     v = np.asarray(v, dtype=np.float64)
     P = len(windows)
@@ -210,7 +212,7 @@ def matvec_all(points, windows, ell, sigma_f: float, v, bandwidth, cutoff: int, 
         xs = np.ascontiguousarray(X[:, list(w)])
         xt = None if rows is None else np.ascontiguousarray(T[:, list(w)])
         if level == "nfft":
-            outK, outD = nfft_fastsum(xs, v, [cg, cd], int(round(sigma * M)), cutoff, sigma, targets=xt)
+            outK, outD = nfft_fastsum(xs, v, [cg, cd], int(round(sigma * M)), cutoff, sigma, targets=xt, win=win)
         elif level == "ndft":
             if rows is not None:
                 raise ValueError("rows are supported at level 'nfft' only")

@@ -19,9 +19,12 @@
  *  orc_gather_grad : the interpolation and its gradient in the target point
  *                 (the window differentiated).
  *
- * phi is the Kaiser-Bessel window with shape b and cutoff m on a grid of n
- * points per dimension:
+ * phi is the Kaiser-Bessel window (kind 0) with shape b and cutoff m on a grid
+ * of n points per dimension:
  *   phi(x) = sinh(b*sqrt(m^2 - (n x)^2)) / (pi * sqrt(m^2 - (n x)^2)),  |n x| <= m,
+ * or (kind 1, spreading and interpolation only) the exponential of semicircle
+ * (Barnett, Magland, af Klinteberg 2019) with shape beta:
+ *   phi(x) = exp(beta * (sqrt(1 - (n x / m)^2) - 1)),  |n x| <= m,
  * zero outside; phi~ is its 1-periodisation. Grid index l runs over
  * -n/2 .. n/2-1 and is stored at array position l + n/2 (wrapped mod n).
  */
@@ -43,6 +46,21 @@ static double kb(double t, int m, double b)
     double s = sqrt(s2);
     if (s < 1e-8) return b / ORC_PI;           /* limit of sinh(b s)/s as s -> 0 */
     return sinh(b * s) / (ORC_PI * s);
+}
+
+/* Exponential-of-semicircle window as a function of t = n*x (grid units). */
+static double es(double t, int m, double beta)
+{
+    double z = t / (double)m;
+    double s2 = 1.0 - z * z;
+    if (s2 < 0.0) return 0.0;
+    return exp(beta * (sqrt(s2) - 1.0));
+}
+
+/* The window of the given kind (0 Kaiser-Bessel, 1 exponential of semicircle) with its shape. */
+static double window_value(double t, int m, double shape, int kind)
+{
+    return kind == 1 ? es(t, m, shape) : kb(t, m, shape);
 }
 
 int orc_num_threads(void)
@@ -93,13 +111,13 @@ void orc_direct(int64_t N, int d, const float *X, int P, const int *win_off, con
 }
 
 /* Support of phi~(x - l/n) along one axis: l = floor(n x) - m + 1 + t, t = 0..2m-1. */
-static void support(double x, int n, int m, double b, int64_t *idx, double *w)
+static void support(double x, int n, int m, double b, int kind, int64_t *idx, double *w)
 {
     double u = x * n;
     double fl = floor(u);
     for (int t = 0; t < 2 * m; ++t) {
         double l = fl - m + 1 + t;
-        w[t] = kb(u - l, m, b);
+        w[t] = window_value(u - l, m, b, kind);
         int64_t a = ((int64_t)l + n / 2) % n;
         if (a < 0) a += n;
         idx[t] = a;
@@ -112,7 +130,7 @@ static void support(double x, int n, int m, double b, int64_t *idx, double *w)
  * g has n^D entries, index ((a0*n)+a1)*n+a2 for D = 3 (last axis fastest).
  * Threads spread disjoint point ranges into private grids that are summed at the end.
  */
-void orc_spread(int64_t N, int D, const double *x, const double *v, int n, int m, double b, double *g)
+void orc_spread(int64_t N, int D, const double *x, const double *v, int n, int m, double b, int kind, double *g)
 {
     int64_t G = 1;
     for (int t = 0; t < D; ++t) G *= n;
@@ -130,7 +148,7 @@ void orc_spread(int64_t N, int D, const double *x, const double *v, int n, int m
         double w[3][64];
         #pragma omp for schedule(static)
         for (int64_t j = 0; j < N; ++j) {
-            for (int t = 0; t < D; ++t) support(x[j * D + t], n, m, b, idx[t], w[t]);
+            for (int t = 0; t < D; ++t) support(x[j * D + t], n, m, b, kind, idx[t], w[t]);
             int W = 2 * m;
             if (D == 1) {
                 for (int a = 0; a < W; ++a) mine[idx[0][a]] += v[j] * w[0][a];
@@ -157,7 +175,7 @@ void orc_spread(int64_t N, int D, const double *x, const double *v, int n, int m
  * of h[a] * prod_t phi~(x_{i,t} - l_t/n). nh grids are read (h is nh x n^D).
  * out is nh x N.
  */
-void orc_gather(int64_t N, int D, const double *x, int n, int m, double b, int nh, const double *h,
+void orc_gather(int64_t N, int D, const double *x, int n, int m, double b, int kind, int nh, const double *h,
                 double *out)
 {
     int64_t G = 1;
@@ -166,7 +184,7 @@ void orc_gather(int64_t N, int D, const double *x, int n, int m, double b, int n
     for (int64_t i = 0; i < N; ++i) {
         int64_t idx[3][64];
         double w[3][64];
-        for (int t = 0; t < D; ++t) support(x[i * D + t], n, m, b, idx[t], w[t]);
+        for (int t = 0; t < D; ++t) support(x[i * D + t], n, m, b, kind, idx[t], w[t]);
         int W = 2 * m;
         for (int q = 0; q < nh; ++q) {
             const double *hq = h + (size_t)q * (size_t)G;

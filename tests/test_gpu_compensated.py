@@ -47,7 +47,7 @@ def test_compensated_spread_grids_are_closer(torch_cuda):
         d, n = len(w), 2 * wl.bandwidth[s]
         x = np.ascontiguousarray(wl.points[:, list(w)].astype(np.float64))
         gref = np.zeros((n,) * d)
-        _clib.lib().orc_spread(len(x), d, _clib.ptr(x), _clib.ptr(v64), n, 4, window.shape(2.0), _clib.ptr(gref))
+        _clib.lib().orc_spread(len(x), d, _clib.ptr(x), _clib.ptr(v64), n, 4, window.shape(2.0), 0, _clib.ptr(gref))
         e_plain = rel(plain.debug_stage(s, 0, vd), gref)
         e_comp = rel(comp.debug_stage(s, 0, vd), gref)
         assert e_comp < e_plain and e_comp < TOL, (s, e_plain, e_comp)

@@ -69,7 +69,7 @@ def test_stage_spread_and_adjoint(torch_cuda):
         x = np.ascontiguousarray(wl.points[:, list(w)].astype(np.float64))
         g = op.debug_stage(s, 0, vd)
         gref = np.zeros((64,) * 3)
-        _clib.lib().orc_spread(len(x), 3, _clib.ptr(x), _clib.ptr(v64), 64, 4, window.shape(2.0), _clib.ptr(gref))
+        _clib.lib().orc_spread(len(x), 3, _clib.ptr(x), _clib.ptr(v64), 64, 4, window.shape(2.0), 0, _clib.ptr(gref))
         assert rel(g, gref) < TOL, s
         S = op.debug_stage(s, 1, vd)
         Sref = fastsum.nfft_adjoint(x, v64, 32, 64, 4)

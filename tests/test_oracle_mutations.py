@@ -19,7 +19,7 @@ def test_wrong_deconvolution_is_caught(monkeypatch):
     v = rng.standard_normal(100)
     assert _adjoint_err(x, v, 16) < 3e-6
     real = fastsum._phihat_grid
-    monkeypatch.setattr(fastsum, "_phihat_grid", lambda M, n, m, s, d: real(M, n, m, s, d) * (1 + 1e-3 * np.arange(M)[:, None]))
+    monkeypatch.setattr(fastsum, "_phihat_grid", lambda M, n, m, s, d, win="kb": real(M, n, m, s, d, win) * (1 + 1e-3 * np.arange(M)[:, None]))
     assert _adjoint_err(x, v, 16) > 1e-4
 
 
@@ -62,5 +62,5 @@ def test_window_transform_mismatch_is_caught(monkeypatch):
     v = rng.standard_normal(100)
     assert _adjoint_err(x, v, 32) < 3e-6
     real = window.phihat_quadrature
-    monkeypatch.setattr(window, "phihat_quadrature", lambda k, n, m, sigma=2.0: real(k, n, m, 1.5))
+    monkeypatch.setattr(window, "phihat_quadrature", lambda k, n, m, sigma=2.0, **kw: real(k, n, m, 1.5, **kw))
     assert _adjoint_err(x, v, 32) > 1e-3

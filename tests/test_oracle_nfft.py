@@ -17,29 +17,45 @@ def pts3():
     return wl.points.astype(np.float64), wl.vector().astype(np.float64)
 
 
+@pytest.mark.parametrize("win", ["kb", "es"])
 @pytest.mark.parametrize("d", [1, 2, 3])
-def test_adjoint_nfft_vs_exact(d):
-    """Spread + FFT + deconvolution reproduces S_k = sum_j v_j exp(-2 pi i k.x_j) (the inner sums)."""
+def test_adjoint_nfft_vs_exact(d, win):
+    """Spread + FFT + deconvolution reproduces S_k = sum_j v_j exp(-2 pi i k.x_j) (the inner sums),
+    with either window."""
     rng = np.random.default_rng(d)
     x = rng.uniform(-0.22, 0.22, size=(300, d))
     v = rng.standard_normal(300)
     M = 16 if d == 3 else 32
     S = fastsum.adjoint_exact(x, v, M)
     for m, tol in ((4, 3e-6), (6, 3e-10)):
-        Sa = fastsum.nfft_adjoint(x, v, M, 2 * M, m)
+        Sa = fastsum.nfft_adjoint(x, v, M, 2 * M, m, win=win)
         assert rel(Sa, S) < tol
 
 
+@pytest.mark.parametrize("win", ["kb", "es"])
 @pytest.mark.parametrize("d", [1, 2, 3])
-def test_forward_nfft_vs_exact(d):
-    """Deconvolution + zero-padded inverse FFT + interpolation reproduces sum_k d_k exp(2 pi i k.x)."""
+def test_forward_nfft_vs_exact(d, win):
+    """Deconvolution + zero-padded inverse FFT + interpolation reproduces sum_k d_k exp(2 pi i k.x),
+    with either window."""
     rng = np.random.default_rng(10 + d)
     x = rng.uniform(-0.22, 0.22, size=(300, d))
     M = 16 if d == 3 else 32
     dh = rng.standard_normal((M,) * d) + 1j * rng.standard_normal((M,) * d)
     f = fastsum.forward_exact(x, dh).real
     for m, tol in ((4, 3e-6), (6, 3e-10)):
-        assert rel(fastsum.nfft_forward(x, [dh], 2 * M, m)[0], f) < tol
+        assert rel(fastsum.nfft_forward(x, [dh], 2 * M, m, win=win)[0], f) < tol
+
+
+def test_es_and_kb_fast_sums_agree(pts3):
+    """The two windows approximate the same trigonometric sum: their fused products differ by no more
+    than the sum of their window errors."""
+    wl_pts, v = pts3
+    c = kernels.coefficients(0.5, 3, 32, 2, 1 / 16)
+    ref = fastsum.ndft_fastsum(wl_pts, v, [c])[0]
+    kb = fastsum.nfft_fastsum(wl_pts, v, [c], 64, 4)[0]
+    es = fastsum.nfft_fastsum(wl_pts, v, [c], 64, 4, win="es")[0]
+    assert rel(es, ref) < 1e-6 and rel(kb, ref) < 1e-6
+    assert rel(es, kb) <= rel(es, ref) + rel(kb, ref)
 
 
 def test_window_error_decays_with_cutoff(pts3):

@@ -51,6 +51,34 @@ def test_window_shape():
     assert p.argmax() == 500
 
 
+def test_es_phihat_quadrature_high_precision():
+    """Exponential-of-semicircle window: the transform against a 30-digit mpmath (tanh-sinh) quadrature
+    of its definition exp(beta (sqrt(1 - (n x/m)^2) - 1)), beta = 2.30 * 2m at sigma = 2."""
+    mp.mp.dps = 30
+    n, m = 64, 4
+    beta = mp.mpf("2.30") * 2 * m
+    assert window.es_beta(m) == pytest.approx(float(beta), rel=1e-15)
+    for k in (0, 7, 16, 31):
+        f = lambda x: mp.exp(beta * (mp.sqrt(1 - (n * x / m) ** 2) - 1)) * mp.cos(2 * mp.pi * k * x)
+        ref = float(mp.quad(f, [-mp.mpf(m) / n, 0, mp.mpf(m) / n]))
+        assert window.phihat_quadrature([k], n, m, window="es")[0] == pytest.approx(ref, rel=1e-10)
+
+
+def test_es_window_shape_and_partition_of_unity():
+    """ES window: even, peak 1 at the centre, exp(-beta) at the edge of its support, zero outside; and
+    its shifts sum to n phi_hat(0) up to the aliasing of phi_hat at multiples of n (Poisson summation)."""
+    n, m = 64, 4
+    x = np.linspace(-0.1, 0.1, 1001)
+    p = window.phi(x, n, m, window="es")
+    np.testing.assert_allclose(p, p[::-1], rtol=1e-12)
+    assert p[500] == 1.0 and np.all(p[np.abs(x) > m / n] == 0)
+    assert window.phi([m / n], n, m, window="es")[0] == pytest.approx(np.exp(-window.es_beta(m)), rel=1e-12)
+    xs = np.random.default_rng(0).uniform(-0.5, 0.5, 50)
+    l = np.arange(-n // 2 - 8, n // 2 + 8)
+    s = window.phi(xs[:, None] - l[None, :] / n, n, m, window="es").sum(axis=1)
+    np.testing.assert_allclose(s, n * window.phihat_quadrature([0], n, m, window="es")[0], rtol=1e-6)
+
+
 # ---------------------------------------------------------------- kernels ---
 
 def test_kernel_closed_forms():
