@@ -72,7 +72,16 @@ extern "C" {
 #define ADDKER_ELL_SHARED   (-1)   /* sum_s dK/d ell_s v: the derivative for one ell shared by all windows */
 #define ADDKER_SIGMA_F      (-2)   /* dK/d sigma_f v = (2/sigma_f) K v */
 
-#define ADDKER_WIN_KB 0            /* Kaiser-Bessel window (the only one implemented) */
+/* NFFT windows (addker_opts.window), support |n x| <= m (2m grid points per axis); the paper leaves the
+ * window to the NFFT literature (Sec. 3.1):
+ *   ADDKER_WIN_KB  Kaiser-Bessel, phi(x) = sinh(b sqrt(m^2 - (n x)^2)) / (pi sqrt(m^2 - (n x)^2)),
+ *                  b = pi (2 - 1/sigma)
+ *   ADDKER_WIN_ES  exponential of semicircle (Barnett, Magland, af Klinteberg 2019),
+ *                  phi(x) = exp(beta (sqrt(1 - (n x/m)^2) - 1)), beta = 2.30 * 2m * (1 - 1/(2 sigma)) / (3/4)
+ *                  (2.30 * 2m at sigma = 2). Products only: addker_vjp returns ADDKER_EINVAL for it (its
+ *                  derivative is unbounded at the support edge). */
+#define ADDKER_WIN_KB 0
+#define ADDKER_WIN_ES 1
 
 /* Kernel families (addker_opts.kernel):
  *   ADDKER_KERNEL_GAUSS     kappa_s(r) = exp(-r^2/(2 ell_s^2)), derivative kernel (r^2/(2 ell_s^2)) kappa_s,
@@ -95,7 +104,7 @@ typedef struct {
                             ||x^{W_s}|| <= 1/4 - eps_B/2 */
     int    p;            /* regularisation degree (transition polynomial of degree 2p-1); -1 = default
                             max(1, floor(M eps_B + 1/2)); 0 = no regularisation (plain periodic continuation) */
-    int    window;       /* ADDKER_WIN_KB */
+    int    window;       /* ADDKER_WIN_KB (default) or ADDKER_WIN_ES */
     int    kernel;       /* ADDKER_KERNEL_GAUSS (default) or ADDKER_KERNEL_MATERN12 */
     int    compensated;  /* 1: compensated grid accumulation (each atomic add's rounding error, found by the
                             error-free two-sum from the value the add returned, is accumulated in an error

@@ -54,9 +54,10 @@ class AddKer:
     """
 
     KERNELS = {"gauss": native.ADDKER_KERNEL_GAUSS, "matern": native.ADDKER_KERNEL_MATERN12}
+    WINDOWS = {"kb": native.ADDKER_WIN_KB, "es": native.ADDKER_WIN_ES}
 
     def __init__(self, points, windows, ell, sigma_f=1.0, bandwidth=32, cutoff=4, eps_B=1.0 / 16.0,
-                 p=-1, sigma_os=2.0, kernel="gauss", compensated=False):
+                 p=-1, sigma_os=2.0, kernel="gauss", compensated=False, window="kb"):
         L = native.lib()
         pts = _dev_f32(points, "points")
         if pts.dim() != 2:
@@ -76,6 +77,9 @@ class AddKer:
         if kernel not in self.KERNELS:
             raise ValueError(f"kernel must be one of {sorted(self.KERNELS)}")
         opts.kernel = self.KERNELS[kernel]
+        if window not in self.WINDOWS:
+            raise ValueError(f"window must be one of {sorted(self.WINDOWS)}")
+        opts.window = self.WINDOWS[window]
         opts.compensated = 1 if compensated else 0
         opts.stream = _stream_ptr()
         plan = ctypes.c_void_p()
@@ -89,6 +93,7 @@ class AddKer:
         self.cutoff = int(cutoff)
         self.sigma_os = float(sigma_os)
         self.kernel = kernel
+        self.window = window
 
     # -- plumbing ---------------------------------------------------------------------------
     def _ready(self):

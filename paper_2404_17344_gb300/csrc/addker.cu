@@ -436,10 +436,27 @@ double kb_window(double t, int m, double b)
     return (m / s) * (std::exp(b * (s - m)) - std::exp(-b * (s + m))) / (1.0 - std::exp(-2.0 * bm));
 }
 
+// Exponential-of-semicircle window in grid units, peak 1: w(t) = exp(beta (sqrt(1 - (t/m)^2) - 1)).
+double es_window(double t, int m, double beta)
+{
+    const double z = t / m;
+    const double s2 = 1.0 - z * z;
+    if (s2 < 0.0) return 0.0;
+    return std::exp(beta * (std::sqrt(s2) - 1.0));
+}
+
+// Shape of the window of the given kind: b = pi (2 - 1/sigma) (Kaiser-Bessel) or
+// beta = 2.30 * 2m * (1 - 1/(2 sigma)) / (3/4) (exponential of semicircle).
+double window_shape(int kind, int m, double sigma_os)
+{
+    if (kind == ADDKER_WIN_ES) return 2.30 * 2.0 * m * (1.0 - 1.0 / (2.0 * sigma_os)) / 0.75;
+    return M_PI * (2.0 - 1.0 / sigma_os);
+}
+
 // Piece q of the window as a polynomial in u = 2 frac - 1 (t = frac + m - 1 - q): Chebyshev
 // interpolation at kPolyDeg + 1 nodes, converted to monomial coefficients, stored as its even part
 // (coefficients of u^0, u^2, ...) and odd part (u^1, u^3, ...); pieces q >= m are the mirror images.
-void fit_window_poly(int m, double b, WinPoly* out)
+void fit_window_poly(int m, double b, WinPoly* out, int kind = ADDKER_WIN_KB)
 {
     std::memset(out, 0, sizeof(*out));
     const int N = kPolyDeg + 1;
@@ -447,7 +464,8 @@ void fit_window_poly(int m, double b, WinPoly* out)
         double f[kPolyDeg + 1], a[kPolyDeg + 1];
         for (int j = 0; j < N; ++j) {
             double x = std::cos(M_PI * (j + 0.5) / N);
-            f[j] = kb_window((x + 1.0) / 2.0 + m - 1 - q, m, b);
+            const double t = (x + 1.0) / 2.0 + m - 1 - q;
+            f[j] = kind == ADDKER_WIN_ES ? es_window(t, m, b) : kb_window(t, m, b);
         }
         for (int k = 0; k < N; ++k) {
             double acc = 0.0;
@@ -1102,7 +1120,7 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
     if (opts) o = *opts;
     if (N < 1 || N > 0x7fffffffLL || d < 1 || P < 1 || P > kMaxWindows || !win_off || !win_feat || !ell || !bandwidth)
         return ADDKER_EINVAL;
-    if (!(sigma_f > 0.0) || cutoff < 2 || cutoff > 8 || o.window != ADDKER_WIN_KB ||
+    if (!(sigma_f > 0.0) || cutoff < 2 || cutoff > 8 || (o.window != ADDKER_WIN_KB && o.window != ADDKER_WIN_ES) ||
         (o.kernel != ADDKER_KERNEL_GAUSS && o.kernel != ADDKER_KERNEL_MATERN12) ||
         (o.compensated != 0 && o.compensated != 1))
         return ADDKER_EINVAL;
@@ -1137,6 +1155,7 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
     p.eps_B = o.eps_B;
     p.p_opt = o.p;
     p.kernel = o.kernel;
+    p.window = o.window;
     p.comp = o.compensated == 1;
     p.stream = static_cast<cudaStream_t>(o.stream);
     p.feat_off.assign(win_off, win_off + P + 1);
@@ -1147,7 +1166,7 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
     p.dims.resize(P);
     p.kind.resize(P);
     p.n_cells.assign(P, 0);
-    double b_shape = M_PI * (2.0 - 1.0 / o.sigma_os);
+    const double b_shape = window_shape(o.window, cutoff, o.sigma_os);
     for (int s = 0; s < P; ++s) {
         WinDev& w = p.win[s];
         std::memset(&w, 0, sizeof(w));
@@ -1159,7 +1178,7 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
         w.m = cutoff;
         w.b = (float)b_shape;
     }
-    fit_window_poly(cutoff, b_shape, &p.poly);
+    fit_window_poly(cutoff, b_shape, &p.poly, o.window);
     int* keys = nullptr;
     int* flag = nullptr;
     int status = ADDKER_OK;
@@ -1333,6 +1352,7 @@ int addker_vjp(addker_plan* plan, const float* v, const float* w, float* grad_v,
 {
     if (!plan || !v || !w || !grad_v || !grad_theta || !grad_points) return ADDKER_EINVAL;
     Plan& p = plan->p;
+    if (p.window != ADDKER_WIN_KB) return ADDKER_EINVAL;         // needs a window with a bounded derivative
     CS(ensure_slots(p, 1));
     cudaStream_t st = p.stream;
     float* gx = grad_points;
@@ -1571,9 +1591,10 @@ int addker_debug_stage(addker_plan* plan, int window, int stage, const float* v,
             CK(cudaMemsetAsync(w.gerr, 0, sizeof(float) * gsz, st));
         }
         CK(cudaStreamSynchronize(st));
-        // the device window is w = phi * C with C = pi m / sinh(b m); report in phi's normalisation
+        // the device window is w = phi * C with C = pi m / sinh(b m) (Kaiser-Bessel; 1 for the
+        // exponential of semicircle, whose peak is 1); report in phi's normalisation
         double b = M_PI * (2.0 - 1.0 / p.sigma_os);
-        double C = M_PI * w.m / std::sinh(b * w.m);
+        double C = p.window == ADDKER_WIN_ES ? 1.0 : M_PI * w.m / std::sinh(b * w.m);
         double scale = std::pow(C, -w.D);
         std::fill(out, out + full, 0.0);
         for (int64_t i = 0; i < gsz; ++i) {

@@ -38,8 +38,9 @@ constexpr int kMaxBandwidth = 64;
 // kPolyDeg. The window is even, so piece W-1-q is piece q mirrored, P_{W-1-q}(u) = P_q(-u); with
 // P_q(u) = E_q(u^2) + u O_q(u^2) both come from one even and one odd part:
 //   w_q = E_q(u^2) + u O_q(u^2),   w_{W-1-q} = E_q(u^2) - u O_q(u^2),   q < m.
-// Fitted at setup (FP64 Chebyshev interpolation of the normalised Kaiser-Bessel window) to about
-// 1e-7 of the peak; passed by value, so the coefficients sit in the constant bank.
+// Fitted at setup (FP64 Chebyshev interpolation of the window normalised to peak 1: Kaiser-Bessel or
+// exponential of semicircle) to about 1e-7 of the peak; passed by value, so the coefficients sit in
+// the constant bank.
 constexpr int kPolyDeg = 9;
 constexpr int kMaxW = 16;
 constexpr int kHalfCoef = (kPolyDeg + 2) / 2;    // coefficients of E_q and O_q each
@@ -69,7 +70,7 @@ struct WinDev {                          // copied by value into kernel paramete
     int feat[3];                         // feature (column of the points array) of each axis
     int lo[3];                           // grid-array index (l + n/2) of the box origin per axis
     int box[3];
-    float b;                             // Kaiser-Bessel shape pi (2 - 1/sigma)
+    float b;                             // window shape (Kaiser-Bessel b or semicircle beta; host only)
 };
 
 struct Plan {
@@ -78,6 +79,7 @@ struct Plan {
     double sigma_f = 1.0, sigma_os = 2.0, eps_B = 1.0 / 16.0;
     int p_opt = -1;
     int kernel = ADDKER_KERNEL_GAUSS;     // radial profile family (addker_opts.kernel)
+    int window = ADDKER_WIN_KB;           // NFFT window (addker_opts.window)
     bool comp = false;                    // compensated grid accumulation (addker_opts.compensated)
     cudaStream_t stream = nullptr;
     std::vector<int> dims, bandwidth, feat_off, feat;

@@ -3,8 +3,9 @@
 //   spread:  g_l   = sum_j v_j prod_t w(n x_{j,t} - l_t),   l in the support of x_j
 //   gather:  f_i   = sum_l h_l prod_t w(n x_{i,t} - l_t)     for the two grids h^K and h^der
 // (Sec. 3.1, eq. "approx fast sum": the inner sums by an adjoint NFFT, the outer sums by an
-// NFFT). w is the normalised Kaiser-Bessel window (evaluated through its piecewise polynomial
-// form, see WinPoly); the support of x along an axis is floor(n x) - m + 1 .. floor(n x) + m.
+// NFFT). w is the plan's window normalised to peak 1 (Kaiser-Bessel or exponential of semicircle),
+// evaluated through its piecewise polynomial form (WinPoly); the support of x along an axis is
+// floor(n x) - m + 1 .. floor(n x) + m.
 //
 // Points are sorted by grid cell, so all points of a work item share one support box of
 // (2m)^D grid points. The fast kernels (D = 3, m = 4) exploit that:

@@ -21,6 +21,7 @@ ADDKER_ELIMIT = -6
 ADDKER_ELL_SHARED = -1
 ADDKER_SIGMA_F = -2
 ADDKER_WIN_KB = 0
+ADDKER_WIN_ES = 1
 ADDKER_KERNEL_GAUSS = 0
 ADDKER_KERNEL_MATERN12 = 1
 
