@@ -29,7 +29,7 @@
  *   gradients    addker_vjp (w^T K v with respect to v, ell, sigma_f and the points)
  *   solvers      addker_cg (regression system, Sec. 3.3), addker_gp_grad (GP training)
  *   analysis     addker_gsi (global sensitivity indices, Sec. 4)
- *   utilities    addker_prescale, addker_sync, addker_strerror, addker_device_rates, addker_profile,
+ *   utilities    addker_prescale, addker_prescale_cube, addker_sync, addker_strerror, addker_device_rates, addker_profile,
  *                addker_profile_read, addker_debug_stage
  * The additive Matern(1/2) kernel of Sec. 5 is selected by addker_opts.kernel.
  *
@@ -312,6 +312,19 @@ int addker_prescale(const float* X, int64_t N, int d, const int* win_off, const 
  * about 0.2 s of GPU time. ADDKER_ECUDA / ADDKER_ENOMEM on failure.
  */
 int addker_device_rates(double* out, int cap);
+
+/*
+ * Data prescaling of Sec. 3.2 in the paper's own two steps: every feature f is first mapped affinely
+ * from its range [min_f, max_f] onto [-r, r] (the paper: onto [-1/4, 1/4]), then all features are
+ * divided by sqrt(d_max), d_max the longest window; every windowed point then lies in the ball of
+ * radius r. Here r = (1/4 - eps_B/2)(1 - 4e-7), which adds the boundary width eps_B the fast summation
+ * needs and a margin for FP32 rounding. A constant feature maps to 0.
+ * X and Xs: device, N x d float32 row-major (Xs may equal X). factor: host, out, = 4 r / sqrt(d_max): a
+ * length scale chosen for data in [-1/4, 1/4]^d is multiplied by it (the paper's ell / sqrt(d_max)).
+ * ADDKER_EDOMAIN if X holds a non-finite value. Synchronous on the given stream (NULL = legacy default).
+ */
+int addker_prescale_cube(const float* X, int64_t N, int d, const int* win_off, const int* win_feat, int P,
+                         double eps_B, float* Xs, double* factor, void* stream);
 
 /*
  * Plan inspection for tests and benchmarks. Writes up to `cap` int64 values into info:

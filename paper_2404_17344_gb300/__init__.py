@@ -324,17 +324,20 @@ class AddKer:
             pass
 
 
-def prescale(X, windows, eps_B=1.0 / 16.0):
-    """Sec. 3.2 prescaling on the device: returns (scaled copy of X, factor)."""
+def prescale(X, windows, eps_B=1.0 / 16.0, rule="ball"):
+    """Sec. 3.2 prescaling on the device: returns (scaled copy of X, factor).
+    rule "ball": one global factor into the ball of radius 1/4 - eps_B/2 (addker_prescale);
+    rule "cube": the paper's per-feature map onto a cube, then 1/sqrt(d_max) (addker_prescale_cube)."""
     torch = _torch()
     X = _dev_f32(X, "X")
     N, d = int(X.shape[0]), int(X.shape[1])
     off, feat = _csr(windows)
     out = torch.empty_like(X)
     f = ctypes.c_double()
-    native.check(native.lib().addker_prescale(ctypes.c_void_p(X.data_ptr()), N, d, off, feat, len(windows),
-                                              float(eps_B), ctypes.c_void_p(out.data_ptr()), ctypes.byref(f),
-                                              _stream_ptr()), "addker_prescale")
+    fn = {"ball": "addker_prescale", "cube": "addker_prescale_cube"}[rule]
+    native.check(getattr(native.lib(), fn)(ctypes.c_void_p(X.data_ptr()), N, d, off, feat, len(windows),
+                                           float(eps_B), ctypes.c_void_p(out.data_ptr()), ctypes.byref(f),
+                                           _stream_ptr()), fn)
     return out, f.value
 
 

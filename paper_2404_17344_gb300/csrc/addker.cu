@@ -10,6 +10,7 @@
 // A product then runs, per right-hand side: clear grids, spread, forward DFT + multiply,
 // inverse DFT, gather (+ window sum), all on the plan's stream.
 #include <algorithm>
+#include <limits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -316,6 +317,55 @@ __global__ void k_max_norm(const float* __restrict__ X, int64_t N, int d, const 
     }
     for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
     if ((threadIdx.x & 31) == 0) atomicMax(result, __float_as_uint(best));
+}
+
+// Order-preserving atomic min / max of floats through their bit patterns (non-negative floats order
+// like ints, negative ones reversed like unsigned); mm[2f] starts at +inf, mm[2f + 1] at -inf.
+__device__ __forceinline__ void atomic_min_float(float* a, float v)
+{
+    if (v >= 0.f) atomicMin(reinterpret_cast<int*>(a), __float_as_int(v));
+    else atomicMax(reinterpret_cast<unsigned*>(a), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_max_float(float* a, float v)
+{
+    if (v >= 0.f) atomicMax(reinterpret_cast<int*>(a), __float_as_int(v));
+    else atomicMin(reinterpret_cast<unsigned*>(a), __float_as_uint(v));
+}
+
+// Per-feature range of X (N x d row-major): mm[2f] = min_j X[j][f], mm[2f + 1] = max_j X[j][f];
+// *bad = 1 if any value is not finite. Block (feature column chunk): threads stride over rows.
+__global__ void k_feature_range(const float* __restrict__ X, int64_t N, int d, float* __restrict__ mm,
+                                int* __restrict__ bad)
+{
+    const int f = blockIdx.y;
+    float lo = __int_as_float(0x7f800000), hi = -lo;
+    int nonfinite = 0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        const float x = X[j * d + f];
+        if (!isfinite(x)) nonfinite = 1;
+        lo = fminf(lo, x);
+        hi = fmaxf(hi, x);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        nonfinite |= __shfl_xor_sync(0xffffffffu, nonfinite, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_min_float(mm + 2 * f, lo);
+        atomic_max_float(mm + 2 * f + 1, hi);
+        if (nonfinite) atomicOr(bad, 1);
+    }
+}
+
+// Y[j][f] = X[j][f] * scale[f] + shift[f]
+__global__ void k_affine_features(const float* __restrict__ X, int64_t N, int d, const float* __restrict__ scale,
+                                  const float* __restrict__ shift, float* __restrict__ Y)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N * d) return;
+    const int f = (int)(i % d);
+    Y[i] = fmaf(X[i], scale[f], shift[f]);
 }
 
 // dst[i] = src[i], i < n, where one side may be page-locked host memory reached over the CPU-GPU
@@ -1546,6 +1596,69 @@ int addker_prescale(const float* X, int64_t N, int d, const int* win_off, const 
     cudaFree(buf);
     if (e != cudaSuccess) return ADDKER_ECUDA;
     *factor = f;
+    return ADDKER_OK;
+}
+
+int addker_prescale_cube(const float* X, int64_t N, int d, const int* win_off, const int* win_feat, int P,
+                         double eps_B, float* Xs, double* factor, void* stream)
+{
+    if (!X || !Xs || !factor || N < 1 || d < 1 || d > 65535 || P < 1 || !win_off || !win_feat ||
+        !(eps_B > 0.0 && eps_B < 0.5) || win_off[0] != 0)
+        return ADDKER_EINVAL;
+    int dmax = 0;
+    for (int s = 0; s < P; ++s) {
+        if (win_off[s + 1] <= win_off[s]) return ADDKER_EINVAL;
+        for (int q = win_off[s]; q < win_off[s + 1]; ++q) if (win_feat[q] < 0 || win_feat[q] >= d) return ADDKER_EINVAL;
+        dmax = std::max(dmax, win_off[s + 1] - win_off[s]);
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float* mm = nullptr;                                     // 2d range values, 2d affine coefficients, flag
+    CK(cudaMalloc(&mm, sizeof(float) * (4 * (size_t)d + 1)));
+    int* bad = reinterpret_cast<int*>(mm + 4 * (size_t)d);
+    std::vector<float> h(2 * (size_t)d);
+    for (int f = 0; f < d; ++f) {
+        h[2 * f] = std::numeric_limits<float>::infinity();
+        h[2 * f + 1] = -std::numeric_limits<float>::infinity();
+    }
+    int hbad = 0;
+    cudaError_t e = cudaMemcpyAsync(mm, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        const int bx = (int)std::min<int64_t>(64, (N + 255) / 256);
+        k_feature_range<<<dim3(bx, d), 256, 0, st>>>(X, N, d, mm, bad);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), mm, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaFree(mm);
+        return ADDKER_ECUDA;
+    }
+    if (hbad) {
+        cudaFree(mm);
+        return ADDKER_EDOMAIN;
+    }
+    // [min_f, max_f] -> [-r, r] per feature, then / sqrt(d_max); r = (1/4 - eps_B/2) shrunk by 4e-7 so that
+    // FP32 rounding of the map cannot leave the ball
+    const double r = (0.25 - eps_B / 2.0) * (1.0 - 4e-7);
+    const double inv = 1.0 / std::sqrt((double)dmax);
+    std::vector<float> coef(2 * (size_t)d);
+    for (int f = 0; f < d; ++f) {
+        const double lo = h[2 * f], hi = h[2 * f + 1];
+        const double a = hi > lo ? 2.0 * r / (hi - lo) * inv : 0.0;
+        coef[f] = (float)a;
+        coef[d + f] = (float)(hi > lo ? -(lo + hi) / 2.0 * a : 0.0);
+    }
+    e = cudaMemcpyAsync(mm + 2 * (size_t)d, coef.data(), sizeof(float) * coef.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        k_affine_features<<<grid_blocks(N * d, 256), 256, 0, st>>>(X, N, d, mm + 2 * (size_t)d, mm + 3 * (size_t)d, Xs);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(mm);
+    if (e != cudaSuccess) return ADDKER_ECUDA;
+    *factor = 4.0 * r * inv;
     return ADDKER_OK;
 }
 

@@ -57,6 +57,7 @@ SIGNATURES = {
     "addker_free": (_I, [_VP]),
     "addker_strerror": (ctypes.c_char_p, [_I]),
     "addker_prescale": (_I, [_VP, _I64, _I, _VP, _VP, _I, _D, _VP, ctypes.POINTER(_D), _VP]),
+    "addker_prescale_cube": (_I, [_VP, _I64, _I, _VP, _VP, _I, _D, _VP, ctypes.POINTER(_D), _VP]),
     "addker_info": (_I, [_VP, ctypes.POINTER(_I64), _I]),
     "addker_device_rates": (_I, [ctypes.POINTER(_D), _I]),
     "addker_debug_stage": (_I, [_VP, _I, _I, _VP, _VP, _I64]),

@@ -226,6 +226,31 @@ def test_prescale_matches_recipe(torch_cuda):
     np.testing.assert_allclose(Xs.cpu().numpy(), X * np.float32(f), rtol=1e-6)
 
 
+def test_prescale_cube_matches_paper_rule(torch_cuda):
+    """Sec. 3.2 as stated: each feature mapped from its range onto [-r, r], then divided by sqrt(d_max);
+    every windowed point inside the ball of radius r = 1/4 - eps_B/2; a constant feature maps to 0."""
+    torch = torch_cuda
+    from paper_2404_17344_gb300 import prescale
+    rng = np.random.default_rng(9)
+    X = (rng.standard_normal((4000, 7)) * rng.uniform(0.1, 5.0, 7) + rng.uniform(-3, 3, 7)).astype(np.float32)
+    X[:, 5] = 2.5                                               # constant feature
+    wins = [(0, 1, 2), (3, 4), (5, 6)]
+    Xs, f = prescale(torch.from_numpy(X).cuda(), wins, rule="cube")
+    Xs = Xs.cpu().numpy().astype(np.float64)
+    r = (0.25 - 1 / 32) * (1 - 4e-7)
+    X64 = X.astype(np.float64)
+    lo, hi = X64.min(0), X64.max(0)
+    span = np.where(hi > lo, hi - lo, 1.0)
+    ref = np.where(hi > lo, (2 * (X64 - lo) / span - 1) * r, 0.0) / np.sqrt(3)
+    np.testing.assert_allclose(Xs, ref, atol=1e-6 * r)
+    assert f == pytest.approx(4 * r / np.sqrt(3), rel=1e-12)
+    assert max(np.sqrt((Xs[:, list(w)] ** 2).sum(1)).max() for w in wins) <= 0.25 - 1 / 32
+    Xn = X.copy()
+    Xn[3, 2] = np.inf
+    with pytest.raises(Exception):
+        prescale(torch.from_numpy(Xn).cuda(), wins, rule="cube")
+
+
 @pytest.mark.slow
 def test_full_size_sampled_rows(torch_cuda):
     """N = 1e6, d = 9, three windows of 3 (the benchmark workload): GPU outputs on 1500 sampled rows
