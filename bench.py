@@ -493,7 +493,7 @@ def main():
     ap.add_argument("--N", type=int, default=1_000_000)
     ap.add_argument("--cpu-sample", type=int, default=200_000)
     ap.add_argument("--ref-sample", type=int, default=100_000)
-    ap.add_argument("--check-rows", type=int, default=256)
+    ap.add_argument("--check-rows", type=int, default=4096)
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--mode", default="product", choices=["product", "batched", "gp", "cpu"],
                     help="product: the headline fused product; batched: 7 mixed windows x 64 right-hand sides; "
