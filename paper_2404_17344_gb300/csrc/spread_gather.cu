@@ -359,22 +359,14 @@ __device__ __forceinline__ void warp_transpose_reduce(float* v, int lane, int* b
     *held_out = held;
 }
 
+// One 1-D or 2-D spread item (m = 4) by one warp: rhs r reads v (already offset to that rhs).
 template <int D>
-__global__ void __launch_bounds__(kWarps * 32) k_spread_lowd_w8(const int4* __restrict__ items, int nitems,
-                                                               const WinDev* __restrict__ wins,
-                                                               const float* __restrict__ v, int64_t ldv,
-                                                               const WinPoly poly)
+__device__ __forceinline__ void spread_lowd_item(const int4 it, const WinDev& P, const float* __restrict__ v, int r,
+                                                 int lane, const WinPoly& poly)
 {
     constexpr int W = 8;
     constexpr int NV = D == 1 ? W : W * W;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int item = blockIdx.x * kWarps + warp;
-    if (item >= nitems) return;
-    const int4 it = items[item];
-    const WinDev& P = wins[it.w];
     const float4* __restrict__ pts = P.pts + it.x;
-    const int r = blockIdx.y;                                  // right-hand side
-    v += r * ldv;
     float acc[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.f;
@@ -432,6 +424,178 @@ __global__ void __launch_bounds__(kWarps * 32) k_spread_lowd_w8(const int4* __re
             const size_t o = r * P.gsz + (size_t)(ox + a) * P.box[1] + (D >= 2 ? oy + b : 0);
             grid_add(P.grid + o, P.gerr ? P.gerr + o : nullptr, acc[e]);
         }
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kWarps * 32) k_spread_lowd_w8(const int4* __restrict__ items, int nitems,
+                                                               const WinDev* __restrict__ wins,
+                                                               const float* __restrict__ v, int64_t ldv,
+                                                               const WinPoly poly)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * kWarps + warp;
+    if (item >= nitems) return;
+    const int4 it = items[item];
+    const int r = blockIdx.y;                                  // right-hand side
+    spread_lowd_item<D>(it, wins[it.w], v + r * ldv, r, lane, poly);
+}
+
+// Every m = 4 spread item of every window (3-D, 2-D and 1-D, any mix) in one persistent launch: the
+// 3-D units run the pipelined register-tile loop above, the others the one-warp low-d routine; a
+// 3-D unit's first batch is prefetched by the unit before it only when that one is 3-D as well.
+// Unit u takes item (u % nitems + rot) % nitems: with rot = the number of 3-D items the low-d items
+// (latency-bound, few) go first and overlap the 3-D work, whose light items then form the tail.
+__global__ void __launch_bounds__(kWarps * 32, 2) k_spread_w8_all(const int4* __restrict__ items, int nitems,
+                                                              int nunits, int rot, int* __restrict__ counter,
+                                                              const WinDev* __restrict__ wins,
+                                                              const float* __restrict__ v, int64_t ldv,
+                                                              const WinPoly poly)
+{
+    constexpr int W = 8;
+    constexpr int STRIDE = 28;            // 8 + 8 + 8 floats, padded so staging stores avoid conflicts
+    __shared__ __align__(16) float sw[kWarps][32 * STRIDE];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* ws = sw[warp];
+    const int hw = lane >> 4, ah = (lane >> 3) & 1, bh = (lane >> 2) & 1, cq = lane & 3;
+
+    int u = 0;
+    if (lane == 0) u = atomicAdd(counter, 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= nunits) return;
+    int un = 0;
+    if (lane == 0) un = atomicAdd(counter, 1);
+    un = __shfl_sync(0xffffffffu, un, 0);
+    int4 it = items[(u % nitems + rot) % nitems];
+    int r = u / nitems;
+    int4 itn = un < nunits ? items[(un % nitems + rot) % nitems] : make_int4(0, 0, 0, 0);
+    const WinDev* P = wins + it.w;
+    const float4* __restrict__ pts = P->pts + it.x;
+    const float* __restrict__ vr = v + r * ldv;
+    // software pipeline: the next batch's point (and then its v) is in flight during this batch;
+    // `primed`: the current 3-D unit's first batch is already loaded
+    float4 pn = make_float4(0.f, 0.f, 0.f, 0.f);
+    float vn = 0.f;
+    bool primed = false;
+    while (true) {
+        const bool more = un < nunits;
+        if (P->D != 3) {
+            if (P->D == 2) spread_lowd_item<2>(it, *P, vr, r, lane, poly);
+            else spread_lowd_item<1>(it, *P, vr, r, lane, poly);
+            primed = false;
+            if (!more) break;
+            it = itn;
+            r = un / nitems;
+            P = wins + it.w;
+            pts = P->pts + it.x;
+            vr = v + r * ldv;
+            if (lane == 0) un = atomicAdd(counter, 1);
+            un = __shfl_sync(0xffffffffu, un, 0);
+            itn = un < nunits ? items[(un % nitems + rot) % nitems] : make_int4(0, 0, 0, 0);
+            continue;
+        }
+        if (!primed && lane < it.y) {
+            pn = pts[lane];
+            vn = __ldg(vr + __float_as_int(pn.w));
+        }
+        float2 acc[4][2][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][q >> 1][q & 1] = f2(0.f, 0.f);
+        const int count = it.y;
+        const int n = P->n;
+        // the next unit is prefetched only if it is 3-D as well
+        const bool n3 = more && wins[itn.w].D == 3;
+        for (int base = 0; base < count; base += 32) {
+            const float4 p = pn;
+            const float vv = vn;
+            const bool valid = base + lane < count;
+            const bool last = base + 32 >= count;
+            // prefetch: the next batch of this item, or the first batch of the next unit
+            const float4* __restrict__ npts = last ? wins[itn.w].pts + itn.x : pts + base + 32;
+            const int ncount = last ? (n3 ? itn.y : 0) : count - base - 32;
+            if (lane < ncount) pn = npts[lane];
+            float wx[W], wy[W], wz[W];
+            int cx, cy, cz;
+            if (valid) {
+                window_weights<W>(poly, p.x, n, wx, &cx);
+                window_weights<W>(poly, p.y, n, wy, &cy);
+                window_weights<W>(poly, p.z, n, wz, &cz);
+#pragma unroll
+                for (int q = 0; q < W; ++q) wx[q] *= vv;
+            } else {
+#pragma unroll
+                for (int q = 0; q < W; ++q) { wx[q] = 0.f; wy[q] = 0.f; wz[q] = 0.f; }
+            }
+            if (lane < ncount) vn = __ldg((last ? v + (un / nitems) * ldv : vr) + __float_as_int(pn.w));
+            float4* dst = reinterpret_cast<float4*>(ws + lane * STRIDE);
+            dst[0] = make_float4(wx[0], wx[1], wx[2], wx[3]);
+            dst[1] = make_float4(wx[4], wx[5], wx[6], wx[7]);
+            dst[2] = make_float4(wy[0], wy[1], wy[2], wy[3]);
+            dst[3] = make_float4(wy[4], wy[5], wy[6], wy[7]);
+            dst[4] = make_float4(wz[0], wz[1], wz[2], wz[3]);
+            dst[5] = make_float4(wz[4], wz[5], wz[6], wz[7]);
+            __syncwarp();
+            // rows cnt .. 31 hold zeros (lanes without a point stage zero weights), so an odd count is safe
+            const int cnt = min(32, count - base);
+            const float* src = ws + hw * STRIDE;
+#pragma unroll 2
+            for (int j = 0; j < cnt; j += 2, src += 2 * STRIDE) {
+                const float4 xa = *reinterpret_cast<const float4*>(src + 4 * ah);         // a = 4ah .. 4ah+3
+                const float4 yb = *reinterpret_cast<const float4*>(src + 8 + 4 * bh);     // b = 4bh .. 4bh+3
+                const float2 zc = *reinterpret_cast<const float2*>(src + 16 + 2 * cq);    // c = 2cq, 2cq+1
+                const float2 Y[2] = {f2(yb.x, yb.y), f2(yb.z, yb.w)};
+                const float2 Z[2] = {f2(zc.x, zc.x), f2(zc.y, zc.y)};
+                const float2 X[4] = {f2(xa.x, xa.x), f2(xa.y, xa.y), f2(xa.z, xa.z), f2(xa.w, xa.w)};
+                float2 B[2][2];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) B[q >> 1][q & 1] = __fmul2_rn(Y[q >> 1], Z[q & 1]);
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        acc[a][q >> 1][q & 1] = __ffma2_rn(X[a], B[q >> 1][q & 1], acc[a][q >> 1][q & 1]);
+            }
+            __syncwarp();
+        }
+        // sum the halves: half hw keeps the values with i = hw and receives its partner's
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const float2 send = hw ? acc[a][p][0] : acc[a][p][1];
+                float2 keep = hw ? acc[a][p][1] : acc[a][p][0];
+                keep.x += __shfl_xor_sync(0xffffffffu, send.x, 16);
+                keep.y += __shfl_xor_sync(0xffffffffu, send.y, 16);
+                acc[a][p][0] = keep;
+            }
+        // flush: grid index of (a, b, c) relative to the box origin, c = 2cq + hw
+        const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff, cz = (it.z >> 16) & 0xff;
+        const int ox = cx - 3 - P->lo[0], oy = cy - 3 - P->lo[1], oz = cz - 3 - P->lo[2];
+        const int sy = P->box[2], sx = P->box[1] * P->box[2];
+        const size_t o0 = r * P->gsz + (size_t)(ox + 4 * ah) * sx + (size_t)(oy + 4 * bh) * sy + oz + 2 * cq + hw;
+        float* g = P->grid + o0;
+        float* ge = P->gerr ? P->gerr + o0 : nullptr;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const size_t oa = (size_t)a * sx;
+            grid_add(g + oa, ge ? ge + oa : nullptr, acc[a][0][0].x);
+            grid_add(g + oa + sy, ge ? ge + oa + sy : nullptr, acc[a][0][0].y);
+            grid_add(g + oa + 2 * sy, ge ? ge + oa + 2 * sy : nullptr, acc[a][1][0].x);
+            grid_add(g + oa + 3 * sy, ge ? ge + oa + 3 * sy : nullptr, acc[a][1][0].y);
+        }
+        primed = n3;
+        if (!more) break;
+        // advance: the prefetched unit becomes current; take the one after it
+        it = itn;
+        r = un / nitems;
+        P = wins + it.w;
+        pts = P->pts + it.x;
+        vr = v + r * ldv;
+        if (lane == 0) un = atomicAdd(counter, 1);
+        un = __shfl_sync(0xffffffffu, un, 0);
+        itn = un < nunits ? items[(un % nitems + rot) % nitems] : make_int4(0, 0, 0, 0);
     }
 }
 
@@ -667,7 +831,29 @@ cudaError_t launch_spread(const Plan& p, int window, const float* v, int64_t ldv
 {
     int launched = 0;
     const WinDev* wd = p.wins_dev;
-    for (int k = 0; k < kKinds; ++k) {
+    int k0 = 0;
+    if (window < 0) {
+        // the m = 4 kinds (3-D, 1-D, 2-D fast) lie next to each other in the spread list: one persistent
+        // launch for all of them, units taken from a zeroed counter
+        const int lo = p.item_begin_sp[kKindFast3].front(), hi = p.item_begin_sp[kKindLow2].back();
+        const int n3 = p.item_begin_sp[kKindFast3].back() - lo;
+        if (hi > lo) {
+            const int n = hi - lo, units = n * nrhs;
+            if (cudaMemsetAsync(p.counters, 0, sizeof(int), st) != cudaSuccess) return cudaGetLastError();
+            if (n3 == n) {                    // 3-D items only: the kernel without the per-unit branch
+                const int nb = std::min(resident_blocks(k_spread3_w8, kWarps * 32), (units + kWarps - 1) / kWarps);
+                launch_k(false, k_spread3_w8, dim3(nb), dim3(kWarps * 32), 0, st, p.items + lo, n, units, p.counters,
+                         wd, v, ldv, p.poly);
+            } else {
+                const int nb = std::min(resident_blocks(k_spread_w8_all, kWarps * 32), (units + kWarps - 1) / kWarps);
+                launch_k(false, k_spread_w8_all, dim3(nb), dim3(kWarps * 32), 0, st, p.items + lo, n, units, n3,
+                         p.counters, wd, v, ldv, p.poly);
+            }
+            ++launched;
+        }
+        k0 = kKindGen1;
+    }
+    for (int k = k0; k < kKinds; ++k) {
         int lo, hi;
         item_range(p, k, window, &lo, &hi, true);
         if (hi <= lo) continue;
