@@ -41,7 +41,7 @@ __device__ __forceinline__ float2 cmadc(float2 a, float2 w, float2 c)     // c +
 constexpr int kT = 256;                   // threads of the single-block d < 3 transform
 constexpr int kT3 = 128;                  // threads of the d = 3 blocks
 constexpr int kSplit = 4;                 // blocks per x-slab
-constexpr int kTile = 16;                 // columns (ky, kz) per k_xround block
+constexpr int kTile = 8;                  // columns (ky, kz) per k_xround block (16: 2 us slower)
 
 // Pair range [lo, hi) of part `part` when `pairs` pairs are dealt out to kSplit parts.
 __host__ __device__ inline void part_range(int pairs, int part, int* lo, int* hi)
@@ -57,7 +57,7 @@ __host__ __device__ inline void fused3_smem(int b0, int b1, int b2, int M, size_
     const int kw = 2 * ((M / 2 + kSplit - 1) / kSplit);                 // kz columns per k_fwd_yz block
     const int ny = 2 * (((b1 + 1) / 2 + kSplit - 1) / kSplit);           // y rows per k_inv_yz block
     s[0] = sizeof(float2) * (b2 * kw + b1 * M + b1 * kw) + sizeof(float) * b1 * b2;
-    s[1] = sizeof(float2) * (b0 * M + b0 * kTile) + sizeof(float4) * M * kTile;
+    s[1] = sizeof(float2) * (b0 * M + b0 * kTile) + sizeof(float4) * M * kTile + 2 * sizeof(float) * M * kTile;
     s[2] = sizeof(float4) * (M * M + ny * M) + sizeof(float2) * (ny + b2) * M;
 }
 
@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(kT3) k_fwd_yz(const WinDev* __restrict__ wins,
 }
 
 // block = (tile of kTile columns c = (ky, kz), window, rhs). smem: tx[b0][M] float2, ts[b0][kTile]
-// float2, ss[M][kTile] float4.
+// float2, ss[M][kTile] float4, then the tile's multipliers mK[M][kTile], mD[M][kTile] (staged with
+// cp.async beside the tile rather than read from global memory inside the product loop).
 //   S[kx][c] = m_k sum_x tx[x][kx] t[x][c];   B[x][c] = sum_kx conj(tx[x][kx]) S[kx][c]
 // spec_only: write S (multiplied by dconv) to W.spec and stop.
 __global__ void __launch_bounds__(kT3) k_xround(const WinDev* __restrict__ wins, int w0, int spec_only)
@@ -162,10 +163,22 @@ __global__ void __launch_bounds__(kT3) k_xround(const WinDev* __restrict__ wins,
         if (j < cols) cp_async8(ts + i, t + (size_t)x * MM + c0 + j);
         else ts[i] = make_float2(0.f, 0.f);
     }
+    // the tile's multipliers, staged beside it
+    float* mks = reinterpret_cast<float*>(ss + M * kTile);
+    float* mds = mks + M * kTile;
+    {
+        const float* mK = spec_only ? W.dconv : W.bK;
+        const float* mD = spec_only ? W.dconv : W.bD;
+        for (int i = threadIdx.x; i < M * kTile; i += kT3) {
+            const int kx = i / kTile, j = i % kTile;
+            if (j < cols) {
+                cp_async4(mks + i, mK + (size_t)kx * MM + c0 + j);
+                cp_async4(mds + i, mD + (size_t)kx * MM + c0 + j);
+            }
+        }
+    }
     cp_async_wait_all();
     __syncthreads();
-    const float* mK = spec_only ? W.dconv : W.bK;
-    const float* mD = spec_only ? W.dconv : W.bD;
     const int Mh = M / 2;
     for (int o = threadIdx.x; o < Mh * JP; o += kT3) {            // 2x2 blocks (kx, j)
         const int kx = 2 * (o / JP), j = 2 * (o % JP);
@@ -191,7 +204,7 @@ __global__ void __launch_bounds__(kT3) k_xround(const WinDev* __restrict__ wins,
                     continue;
                 }
                 const size_t k = (size_t)(kx + rr) * MM + c0 + j + q;
-                const float a = __ldg(mK + k), d = __ldg(mD + k);
+                const float a = mks[(kx + rr) * kTile + j + q], d = mds[(kx + rr) * kTile + j + q];
                 const float4 v = make_float4(a * acc[rr][q].x, a * acc[rr][q].y, d * acc[rr][q].x, d * acc[rr][q].y);
                 if (spec_only) W.spec[k] = v;
                 else ss[(kx + rr) * kTile + j + q] = v;
