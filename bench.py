@@ -273,6 +273,17 @@ def run_ours(args, rank, world, local_rank):
     from paper_2404_17344_gb300 import device_rates
     rates = device_rates()
 
+    # the spread's grid flush against the measured L2 atomic rate: one atomic add per box value (W^3) per
+    # work item (every window here is 3-D with m = 4)
+    sp_ms, sp_launches = stage["spread"]
+    atomics = op.info()["items"] * W3
+    sp_s = sp_ms / 1e3 / max(1, sp_launches)
+    atomics_line = {"kernel": "spread", "atomic_adds_per_launch": atomics,
+                    "achieved_gops": atomics / sp_s / 1e9, "peak_gops": rates["global_atomic_gops"],
+                    "frac": atomics / sp_s / 1e9 / rates["global_atomic_gops"],
+                    "note": "grid flush: one float atomic add per box value per work item; peak = measured "
+                            "rate into an L2-resident grid (device_rates)"}
+
     # CPU oracle baseline, bounded sample
     sample = min(N, args.cpu_sample)
     cpu_sec = cpu_oracle_step(wl, v_np, sample) * (N / sample)
@@ -309,6 +320,7 @@ def run_ours(args, rank, world, local_rank):
                         "frac_of_measured": achieved / rates["ffma2_tflops"] if rates["ffma2_tflops"] > 0 else None,
                         "peak_measured_source": "packed FFMA2 microbenchmark (addker_device_rates) at "
                                                 f"{rates['sm_mhz_under_load']:.0f} MHz, after the timed region"},
+           "roofline_atomics": atomics_line,
            "roofline_hbm": {"achieved": hbm_bytes / (ms_per_step / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                             "frac": hbm_bytes / (ms_per_step / 1e3) / 1e9 / hbm_peak,
                             "note": f"algorithmic bytes of the whole step, {pk_kind} copy bandwidth"},
