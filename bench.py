@@ -260,8 +260,9 @@ def run_ours(args, rank, world, local_rank):
         try:
             import hashlib
             rec = json.load(open(tfile))
-            src = open(os.path.join(ROOT, rec["source"]), "rb").read()
-            if hashlib.sha256(src).hexdigest() == rec["source_sha256"]:
+            srcs = rec.get("sources") or {rec["source"]: rec["source_sha256"]}
+            if all(hashlib.sha256(open(os.path.join(ROOT, f), "rb").read()).hexdigest() == h
+                   for f, h in srcs.items()):
                 traffic = rec["bytes_per_launch"]
         except Exception:
             traffic = None
