@@ -106,9 +106,9 @@ typedef struct {
                             max(1, floor(M eps_B + 1/2)); 0 = no regularisation (plain periodic continuation) */
     int    window;       /* ADDKER_WIN_KB (default) or ADDKER_WIN_ES */
     int    kernel;       /* ADDKER_KERNEL_GAUSS (default) or ADDKER_KERNEL_MATERN12 */
-    int    compensated;  /* 1: compensated grid accumulation (each atomic add's rounding error, found by the
-                            error-free two-sum from the value the add returned, is accumulated in an error
-                            grid that the forward transform adds back); 0 (default): plain FP32 adds */
+    int    compensated;  /* 1: compensated grid accumulation: the spread's FP32 tile sums are added into an
+                            FP64 grid (no rounding error from the order of the atomic adds), which the
+                            forward transform rounds once to FP32; 0 (default): plain FP32 adds */
     void*  stream;       /* cudaStream_t for every product of this plan; NULL = legacy default stream */
 } addker_opts;
 
@@ -307,8 +307,9 @@ int addker_prescale(const float* X, int64_t N, int d, const int* win_off, const 
  *   out[2] FFMA TFLOP/s   out[3] packed FFMA2 TFLOP/s (an FMA counts 2 flops)
  *   out[4] shared-memory float atomic adds, 10^9/s (distinct words)
  *   out[5] global float atomic adds into a 1 MiB L2-resident grid, 10^9/s (rows of 32 words)
- *   out[6] milliseconds of the FFMA launch.
- * Writes up to `cap` values (host doubles) and returns the number available (7); synchronous,
+ *   out[6] milliseconds of the FFMA launch
+ *   out[7] global double atomic adds into a 2 MiB L2-resident grid, 10^9/s (rows of 32 words).
+ * Writes up to `cap` values (host doubles) and returns the number available (8); synchronous,
  * about 0.2 s of GPU time. ADDKER_ECUDA / ADDKER_ENOMEM on failure.
  */
 int addker_device_rates(double* out, int cap);

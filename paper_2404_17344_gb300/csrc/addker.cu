@@ -896,20 +896,20 @@ int ensure_slots(Plan& p, int want)
     for (int s = 0; s < p.P; ++s) {
         WinDev& w = p.win[s];
         float* grid;
-        float* gerr = nullptr;
+        double* grid64 = nullptr;
         float2* hh;
         float4 *b1, *b2;
         CS(take(&grid, r * w.gsz));
         if (p.comp) {
-            CS(take(&gerr, r * w.gsz));
-            CK(cudaMemsetAsync(gerr, 0, sizeof(float) * (size_t)(r * w.gsz), p.stream));
+            CS(take(&grid64, r * w.gsz));
+            CK(cudaMemsetAsync(grid64, 0, sizeof(double) * (size_t)(r * w.gsz), p.stream));
         }
         CS(take(&hh, r * w.gsz));
         CS(take(&b1, r * w.b1sz));
         CS(take(&b2, r * w.b2sz));
         CK(cudaMemsetAsync(grid, 0, sizeof(float) * (size_t)(r * w.gsz), p.stream));
         w.grid = grid;
-        w.gerr = gerr;
+        w.grid64 = grid64;
         w.h = hh;
         w.buf1 = b1;
         w.buf2 = b2;
@@ -1696,12 +1696,14 @@ int addker_debug_stage(addker_plan* plan, int window, int stage, const float* v,
     CK(cudaMemsetAsync(w.grid, 0, sizeof(float) * gsz, st));
     CK(launch_spread(p, window, v, p.N, 1, st));                     // slot 0
     if (stage == 0) {
-        std::vector<float> g(gsz), ge(w.gerr ? gsz : 0);
-        CK(cudaMemcpyAsync(g.data(), w.grid, sizeof(float) * gsz, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemsetAsync(w.grid, 0, sizeof(float) * gsz, st));        // products expect a zeroed grid
-        if (w.gerr) {
-            CK(cudaMemcpyAsync(ge.data(), w.gerr, sizeof(float) * gsz, cudaMemcpyDeviceToHost, st));
-            CK(cudaMemsetAsync(w.gerr, 0, sizeof(float) * gsz, st));
+        std::vector<float> g(gsz);
+        std::vector<double> g64(w.grid64 ? gsz : 0);
+        if (w.grid64) {
+            CK(cudaMemcpyAsync(g64.data(), w.grid64, sizeof(double) * gsz, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemsetAsync(w.grid64, 0, sizeof(double) * gsz, st));    // products expect a zeroed grid
+        } else {
+            CK(cudaMemcpyAsync(g.data(), w.grid, sizeof(float) * gsz, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemsetAsync(w.grid, 0, sizeof(float) * gsz, st));
         }
         CK(cudaStreamSynchronize(st));
         // the device window is w = phi * C with C = pi m / sinh(b m) (Kaiser-Bessel; 1 for the
@@ -1716,13 +1718,13 @@ int addker_debug_stage(addker_plan* plan, int window, int stage, const float* v,
             int64_t idx = a0;
             if (w.D >= 2) idx = idx * w.n + a1;
             if (w.D >= 3) idx = idx * w.n + a2;
-            out[idx] = ((double)g[i] + (w.gerr ? (double)ge[i] : 0.0)) * scale;
+            out[idx] = (w.grid64 ? g64[i] : (double)g[i]) * scale;
         }
         return ADDKER_OK;
     }
     CK(launch_transforms(p, window, 1, st, nullptr, true));
     CK(cudaMemsetAsync(w.grid, 0, sizeof(float) * gsz, st));        // d = 3: the inverse pass that clears it did not run
-    if (w.gerr) CK(cudaMemsetAsync(w.gerr, 0, sizeof(float) * gsz, st));
+    if (w.grid64) CK(cudaMemsetAsync(w.grid64, 0, sizeof(double) * gsz, st));
     std::vector<float4> s(md);
     CK(cudaMemcpyAsync(s.data(), w.spec, sizeof(float4) * md, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

@@ -53,7 +53,8 @@ struct WinPoly {
 struct WinDev {                          // copied by value into kernel parameter space
     const float4* pts;
     float* grid;
-    float* gerr;                         // compensation grid (same layout as grid) or NULL
+    double* grid64;                      // compensated mode: the spread grid accumulated in FP64 (same
+                                         // layout as grid, which it replaces) or NULL
     float2* h;
     float4* buf1;
     float4* buf2;
@@ -188,20 +189,13 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // the wait in every warp cost them more than the overlap saved.
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 
-// Add x to the grid value *g. With an error grid e (compensated accumulation), the rounding error of
-// the add goes to *e: the atomic returns the old value a and stores fl(a + x), so the error-free
-// two-sum (Knuth) of a and x recovers that error exactly; the forward transform adds e back to g.
-__device__ __forceinline__ void grid_add(float* g, float* e, float x)
+// Add x to the grid value: into the FP32 grid g, or with compensated accumulation into the FP64 grid
+// g64 (when not NULL), whose sum carries no rounding error of the accumulation order (each term is an
+// FP32 value; 10^4 of them add exactly to within 1e-12 relative in FP64).
+__device__ __forceinline__ void grid_add(float* g, double* g64, float x)
 {
-    if (e == nullptr) {
-        atomicAdd(g, x);
-        return;
-    }
-    const float a = atomicAdd(g, x);
-    const float s = a + x;
-    const float bv = s - a;
-    const float err = (a - (s - bv)) + (x - bv);
-    atomicAdd(e, err);
+    if (g64) atomicAdd(g64, (double)x);
+    else atomicAdd(g, x);
 }
 
 // ---- device window weights ------------------------------------------------------------

@@ -86,13 +86,14 @@ __global__ void __launch_bounds__(kT3) k_fwd_yz(const WinDev* __restrict__ wins,
     for (int i = threadIdx.x; i < b2 * kw; i += kT3) cp_async8(tz + i, W.twf[2] + (i / kw) * M + kb + i % kw);
     for (int i = threadIdx.x; i < b1 * M; i += kT3) cp_async8(ty + i, W.twf[1] + i);
     grid_dep_wait();                                           // the spread grid is complete from here on
-    const float* g = W.grid + r * W.gsz + (size_t)x * b1 * b2;
-    for (int i = threadIdx.x; i < b1 * b2; i += kT3) cp_async4(gs + i, g + i);
-    cp_async_wait_all();
-    if (W.gerr) {                                              // compensated grid: add the error grid
-        const float* ge = W.gerr + r * W.gsz + (size_t)x * b1 * b2;
-        for (int i = threadIdx.x; i < b1 * b2; i += kT3) gs[i] += ge[i];
+    if (W.grid64) {                                            // compensated: the FP64 grid, rounded once
+        const double* g = W.grid64 + r * W.gsz + (size_t)x * b1 * b2;
+        for (int i = threadIdx.x; i < b1 * b2; i += kT3) gs[i] = (float)g[i];
+    } else {
+        const float* g = W.grid + r * W.gsz + (size_t)x * b1 * b2;
+        for (int i = threadIdx.x; i < b1 * b2; i += kT3) cp_async4(gs + i, g + i);
     }
+    cp_async_wait_all();
     __syncthreads();
     // phase 1: rows y (2 per thread, clamped), columns k (2 per thread)
     const int nb1 = (b1 + 1) / 2;
@@ -272,12 +273,13 @@ __global__ void __launch_bounds__(kT3) k_inv_yz(const WinDev* __restrict__ wins,
     for (int i = threadIdx.x; i < b2 * M; i += kT3) cp_async8(tz + i, W.twf[2] + i);
     grid_dep_wait();
     for (int i = threadIdx.x; i < MM; i += kT3) cp_async16(bs + i, B + i);
-    float* g = W.grid + r * W.gsz + (size_t)x * b1 * b2 + (size_t)yb * b2;
     const int zrows = min(ny, b1 - yb);
-    for (int i = threadIdx.x; i < zrows * b2; i += kT3) g[i] = 0.f;
-    if (W.gerr) {
-        float* ge = W.gerr + r * W.gsz + (size_t)x * b1 * b2 + (size_t)yb * b2;
-        for (int i = threadIdx.x; i < zrows * b2; i += kT3) ge[i] = 0.f;
+    if (W.grid64) {
+        double* g = W.grid64 + r * W.gsz + (size_t)x * b1 * b2 + (size_t)yb * b2;
+        for (int i = threadIdx.x; i < zrows * b2; i += kT3) g[i] = 0.0;
+    } else {
+        float* g = W.grid + r * W.gsz + (size_t)x * b1 * b2 + (size_t)yb * b2;
+        for (int i = threadIdx.x; i < zrows * b2; i += kT3) g[i] = 0.f;
     }
     cp_async_wait_all();
     __syncthreads();
@@ -383,15 +385,16 @@ __global__ void __launch_bounds__(kT) k_small_transform(const WinDev* __restrict
     const float2* tf0 = stw ? tws : W.twf[0];
     const float2* tf1 = stw ? tws + b0 * M : W.twf[1];
     grid_dep_wait();
-    for (int i = threadIdx.x; i < b0 * b1; i += kT) cp_async4(gs + i, grid + i);
-    cp_async_wait_all();
-    for (int i = threadIdx.x; i < b0 * b1; i += kT) grid[i] = 0.f;     // each thread clears what it copied
-    if (W.gerr) {                                              // compensated grid: add and clear the errors
-        float* ge = W.gerr + r * W.gsz;
+    if (W.grid64) {                                            // compensated: the FP64 grid, rounded once
+        double* g64 = W.grid64 + r * W.gsz;
         for (int i = threadIdx.x; i < b0 * b1; i += kT) {
-            gs[i] += ge[i];
-            ge[i] = 0.f;
+            gs[i] = (float)g64[i];
+            g64[i] = 0.0;                                      // each thread clears what it read
         }
+    } else {
+        for (int i = threadIdx.x; i < b0 * b1; i += kT) cp_async4(gs + i, grid + i);
+        cp_async_wait_all();
+        for (int i = threadIdx.x; i < b0 * b1; i += kT) grid[i] = 0.f;     // each thread clears what it copied
     }
     __syncthreads();
     if (D == 1) {

@@ -71,8 +71,8 @@ int gsi_run(Plan& p, const float* v, int cap, int* feats, double* rho, double* t
     for (int s = 0; s < p.P && e == cudaSuccess; ++s) {
         const WinDev& w = p.win[s];
         // the spectrum-only pass skips the inverse that clears d = 3 grids
-        if (w.D == 3) e = cudaMemsetAsync(w.grid, 0, sizeof(float) * (size_t)w.gsz, st);
-        if (w.D == 3 && w.gerr && e == cudaSuccess) e = cudaMemsetAsync(w.gerr, 0, sizeof(float) * (size_t)w.gsz, st);
+        if (w.D == 3 && w.grid64) e = cudaMemsetAsync(w.grid64, 0, sizeof(double) * (size_t)w.gsz, st);
+        else if (w.D == 3) e = cudaMemsetAsync(w.grid, 0, sizeof(float) * (size_t)w.gsz, st);
         int64_t tot = 1;
         for (int t = 0; t < w.D; ++t) tot *= w.M;
         const int nb = (int)std::min<int64_t>(1024, (tot + kT - 1) / kT);

@@ -7,8 +7,8 @@
 //   FFMA   8 independent FMA chains per thread, 2048 threads per SM;
 //   FFMA2  the same with packed two-wide FMAs (the form the product's inner loops use);
 //   shared atomics: every thread adds into its own shared word (distinct banks within a warp);
-//   global atomic adds: warps add rows of 32 consecutive floats into a 1 MiB grid (L2-resident),
-//          the access shape of a tile flush.
+//   global atomic adds: warps add rows of 32 consecutive floats (or doubles) into a 1 MiB (2 MiB)
+//          grid (L2-resident), the access shape of a tile flush.
 // The SM clock under load comes from clock64() against the global timer inside the FFMA kernel.
 #include <algorithm>
 #include <vector>
@@ -105,6 +105,21 @@ __global__ void __launch_bounds__(kRateThreads) k_rate_global_atomic(float* grid
     }
 }
 
+// the same access shape with double atomic adds (an FP64 grid accumulates without rounding error in
+// practice); grid of 2^18 doubles
+__global__ void __launch_bounds__(kRateThreads) k_rate_global_atomic64(double* grid, int iters)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const unsigned row = (warp * 97u + (unsigned)(it * kUnroll + u) * 31u) & ((1u << 13) - 1u);
+            atomicAdd(grid + row * 32u + lane, 1.0);
+        }
+    }
+}
+
 struct Buf {
     void* p = nullptr;
     ~Buf() { cudaFree(p); }
@@ -124,7 +139,7 @@ extern "C" int addker_device_rates(double* out, int cap)
     const int64_t threads = (int64_t)blocks * kRateThreads;
     Buf o, c, g;
     if (cudaMalloc(&o.p, sizeof(float) * threads) != cudaSuccess || cudaMalloc(&c.p, sizeof(long long) * 2 * blocks) != cudaSuccess ||
-        cudaMalloc(&g.p, sizeof(float) << 18) != cudaSuccess) {
+        cudaMalloc(&g.p, sizeof(double) << 18) != cudaSuccess) {
         cudaGetLastError();
         return ADDKER_ENOMEM;
     }
@@ -140,7 +155,7 @@ extern "C" int addker_device_rates(double* out, int cap)
         if (e0) cudaEventDestroy(e0);
         return ADDKER_ECUDA;
     }
-    cudaError_t err = cudaMemsetAsync(gf, 0, sizeof(float) << 18, st);
+    cudaError_t err = cudaMemsetAsync(gf, 0, sizeof(double) << 18, st);
     // the median of 3 timed launches after one warm-up launch, in ms
     auto timed = [&](auto launch) -> double {
         std::vector<double> ms;
@@ -166,6 +181,9 @@ extern "C" int addker_device_rates(double* out, int cap)
     const double t_fma2 = timed([&] { k_rate_ffma2<<<blocks, kRateThreads, 0, st>>>(of, it_fma, a, b); });
     const double t_sat = timed([&] { k_rate_shared_atomic<<<blocks, kRateThreads, 0, st>>>(of, it_atom); });
     const double t_red = timed([&] { k_rate_global_atomic<<<blocks, kRateThreads, 0, st>>>(gf, it_red); });
+    if (err == cudaSuccess) err = cudaMemsetAsync(gf, 0, sizeof(double) << 18, st);
+    const double t_red64 =
+        timed([&] { k_rate_global_atomic64<<<blocks, kRateThreads, 0, st>>>(reinterpret_cast<double*>(gf), it_red); });
     cudaStreamDestroy(st);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -178,7 +196,7 @@ extern "C" int addker_device_rates(double* out, int cap)
         if (hc[2 * i + 1] > 0) mhz.push_back(1e3 * (double)hc[2 * i] / (double)hc[2 * i + 1]);
     std::sort(mhz.begin(), mhz.end());
     const double fmas = (double)threads * it_fma * kUnroll * kChains;
-    const double vals[7] = {
+    const double vals[8] = {
         (double)nsm,
         mhz.empty() ? 0.0 : mhz[mhz.size() / 2],
         2.0 * fmas / (t_fma * 1e-3) / 1e12,               // FFMA TFLOP/s
@@ -186,7 +204,8 @@ extern "C" int addker_device_rates(double* out, int cap)
         (double)threads * it_atom * kUnroll / (t_sat * 1e-3) / 1e9,   // shared atomics, G/s
         (double)threads * it_red * kUnroll / (t_red * 1e-3) / 1e9,    // global atomic adds, G/s
         t_fma,
+        (double)threads * it_red * kUnroll / (t_red64 * 1e-3) / 1e9,  // global double atomic adds, G/s
     };
-    for (int i = 0; i < cap && i < 7; ++i) out[i] = vals[i];
-    return 7;
+    for (int i = 0; i < cap && i < 8; ++i) out[i] = vals[i];
+    return 8;
 }

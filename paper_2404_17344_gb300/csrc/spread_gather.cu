@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_spread3_w8(const int4* __res
         const int sy = P->box[2], sx = P->box[1] * P->box[2];
         const size_t o0 = r * P->gsz + (size_t)(ox + 4 * ah) * sx + (size_t)(oy + 4 * bh) * sy + oz + 2 * cq + hw;
         float* g = P->grid + o0;
-        float* ge = P->gerr ? P->gerr + o0 : nullptr;
+        double* ge = P->grid64 ? P->grid64 + o0 : nullptr;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const size_t oa = (size_t)a * sx;
@@ -422,7 +422,7 @@ __device__ __forceinline__ void spread_lowd_item(const int4 it, const WinDev& P,
             const int idx = base + e;
             const int a = D == 1 ? idx : idx / W, b = D == 1 ? 0 : idx % W;
             const size_t o = r * P.gsz + (size_t)(ox + a) * P.box[1] + (D >= 2 ? oy + b : 0);
-            grid_add(P.grid + o, P.gerr ? P.gerr + o : nullptr, acc[e]);
+            grid_add(P.grid + o, P.grid64 ? P.grid64 + o : nullptr, acc[e]);
         }
     }
 }
@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_spread_w8_all(const int4* __
         const int sy = P->box[2], sx = P->box[1] * P->box[2];
         const size_t o0 = r * P->gsz + (size_t)(ox + 4 * ah) * sx + (size_t)(oy + 4 * bh) * sy + oz + 2 * cq + hw;
         float* g = P->grid + o0;
-        float* ge = P->gerr ? P->gerr + o0 : nullptr;
+        double* ge = P->grid64 ? P->grid64 + o0 : nullptr;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const size_t oa = (size_t)a * sx;
@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(128) k_spread_generic(const int4* __restrict__
         if (D == 2) { a = i / W; bb = i % W; }
         if (D == 3) { a = i / (W * W); bb = (i / W) % W; cc = i % W; }
         const size_t g = ((size_t)(ox + a) * P.box[1] + (D >= 2 ? oy + bb : 0)) * P.box[2] + (D >= 3 ? oz + cc : 0);
-        if (box[i] != 0.f) grid_add(P.grid + r * P.gsz + g, P.gerr ? P.gerr + r * P.gsz + g : nullptr, box[i]);
+        if (box[i] != 0.f) grid_add(P.grid + r * P.gsz + g, P.grid64 ? P.grid64 + r * P.gsz + g : nullptr, box[i]);
     }
 }
 
