@@ -25,7 +25,7 @@ namespace addker {
 
 namespace {
 
-constexpr int kWarps = 8;                 // warps per block in the item kernels
+constexpr int kWarps = 4;                 // warps per block in the item kernels (8: 2% slower)
 
 // ----------------------------------------------------------------------------------
 // Packed FP32 pairs (one instruction, two FMAs): the fast kernels keep their accumulators in
@@ -45,7 +45,7 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // ahead, and loads the first batch of the next unit while it finishes the current one, so neither
 // the chain item -> points -> v at the start of an item nor the drain of the atomic adds at its end
 // stalls the warp. Unit u is item u % nitems of right-hand side u / nitems.
-__global__ void __launch_bounds__(kWarps * 32, 2) k_spread3_w8(const int4* __restrict__ items, int nitems,
+__global__ void __launch_bounds__(kWarps * 32, 4) k_spread3_w8(const int4* __restrict__ items, int nitems,
                                                               int nunits, int* __restrict__ counter,
                                                               const WinDev* __restrict__ wins,
                                                               const float* __restrict__ v, int64_t ldv,
@@ -308,7 +308,7 @@ __device__ __forceinline__ void gather3_item(const int4 it, const WinDev& P, flo
 }
 
 template <bool WK, bool WD>
-__global__ void __launch_bounds__(kWarps * 32, 2) k_gather3_w8(const int4* __restrict__ items, int nitems,
+__global__ void __launch_bounds__(kWarps * 32, 4) k_gather3_w8(const int4* __restrict__ items, int nitems,
                                                               const WinDev* __restrict__ wins, GatherArgs g,
                                                               const WinPoly poly)
 {
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_spread_lowd_w8(const int4* __re
 // 3-D unit's first batch is prefetched by the unit before it only when that one is 3-D as well.
 // Unit u takes item (u % nitems + rot) % nitems: with rot = the number of 3-D items the low-d items
 // (latency-bound, few) go first and overlap the 3-D work, whose light items then form the tail.
-__global__ void __launch_bounds__(kWarps * 32, 2) k_spread_w8_all(const int4* __restrict__ items, int nitems,
+__global__ void __launch_bounds__(kWarps * 32, 4) k_spread_w8_all(const int4* __restrict__ items, int nitems,
                                                               int nunits, int rot, int* __restrict__ counter,
                                                               const WinDev* __restrict__ wins,
                                                               const float* __restrict__ v, int64_t ldv,
@@ -680,7 +680,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_gather_lowd_w8(const int4* __re
 // Every m = 4 item of every window in one launch (items of the 3-D, 1-D and 2-D kinds are contiguous):
 // each warp takes the routine of its item's dimension, so mixed windows share one grid and one tail.
 template <bool WK, bool WD>
-__global__ void __launch_bounds__(kWarps * 32, 2) k_gather_w8_all(const int4* __restrict__ items, int nitems,
+__global__ void __launch_bounds__(kWarps * 32, 4) k_gather_w8_all(const int4* __restrict__ items, int nitems,
                                                                  const WinDev* __restrict__ wins, GatherArgs g,
                                                                  const WinPoly poly)
 {
