@@ -15,8 +15,8 @@ kernel kappa_derM(r) = (r/ell) exp(-r/ell), so that dK/d ell_s v = sigma_f^2 (1/
 exp(-r/ell) at r = 0 stays (no near-field correction, which the paper does not describe), so its
 coefficients decay slowly and the Fourier approximation is far less accurate than the Gaussian's.
 
-Regularisation (Sec. 3.1: the kernel is periodised by "a smooth transition" at
-the edges, after Potts-Steidl; the paper does not write it down). Reading: with
+Regularisation (Sec. 3.1: a smoother periodisation, the kernel smoothed near the
+boundary of the period, after Potts-Steidl; the paper does not write it down). Reading: with
 a = 1/2 - eps_B the regularised radial profile is
 
     K_R(r) = kappa(r)           r <= a

@@ -1,8 +1,8 @@
 """Windows of the NFFT, FP64: Kaiser-Bessel (default) and exponential of semicircle. Test infrastructure only.
 
 The paper leaves the NFFT window, the oversampling factor and the cutoff open
-("controlled by several parameters, which we do not further discuss", Sec. 3.1)
-and points to the NFFT literature (Plonka, Potts, Steidl, Tasche). The reading
+(Sec. 3.1 does not discuss the NFFT's accuracy parameters) and points to the NFFT
+literature (Plonka, Potts, Steidl, Tasche). The reading
 taken here is the Kaiser-Bessel window with oversampling sigma = 2 and cutoff m:
 
     phi(x) = sinh(b sqrt(m^2 - (n x)^2)) / (pi sqrt(m^2 - (n x)^2)),   |x| <= m/n,
