@@ -258,14 +258,18 @@ class AddKer:
     AUTOTUNE_CHUNKS = (64, 128, 256, 512, 1024)
 
     def autotune(self, v):
-        """Time the fused product on v ((N,) or (N, nrhs)) for each work-item size in AUTOTUNE_CHUNKS and
-        keep the fastest. Returns (chosen chunk, {chunk: ms per product})."""
+        """Time the fused product on v ((N,) or (N, nrhs)) for each work-item size in AUTOTUNE_CHUNKS (one
+        size for both kernels), then for each spread size with the gather's fixed, and keep the fastest.
+        Returns (gather chunk, {chunk: ms per product} of the joint phase); the spread's size is
+        info()["chunk_spread"]."""
         vv, nrhs = self._rhs(v)
         chosen = ctypes.c_int(0)
-        times = (ctypes.c_double * len(self.AUTOTUNE_CHUNKS))()
+        nc = len(self.AUTOTUNE_CHUNKS)
+        times = (ctypes.c_double * (2 * nc))()
         native.check(self._ready().addker_autotune(self._plan, ctypes.c_void_p(vv.data_ptr()), nrhs,
                                                     ctypes.byref(chosen), times, len(times)), "addker_autotune")
-        return chosen.value, dict(zip(self.AUTOTUNE_CHUNKS, list(times)))
+        self.autotune_spread_times = dict(zip(self.AUTOTUNE_CHUNKS, list(times)[nc:]))
+        return chosen.value, dict(zip(self.AUTOTUNE_CHUNKS, list(times)[:nc]))
 
     STAGES = ("clear", "spread", "transform", "gather", "window_sum")
 
@@ -286,7 +290,7 @@ class AddKer:
         native.check(native.lib().addker_sync(self._plan), "addker_sync")
 
     def info(self):
-        cap = 8 + 4 * self.P
+        cap = 9 + 4 * self.P
         buf = (ctypes.c_int64 * cap)()
         n = native.lib().addker_info(self._plan, buf, cap)
         vals = list(buf[:n])
@@ -294,7 +298,8 @@ class AddKer:
         return {"N": vals[0], "P": vals[1], "items": vals[2], "device_bytes": vals[3],
                 "windows": [dict(d=vals[4 + 4 * s], M=vals[5 + 4 * s], n=vals[6 + 4 * s], cells=vals[7 + 4 * s])
                             for s in range(self.P)],
-                "slots": vals[e], "graphs": vals[e + 1], "graph_replays": vals[e + 2], "chunk": vals[e + 3]}
+                "slots": vals[e], "graphs": vals[e + 1], "graph_replays": vals[e + 2], "chunk": vals[e + 3],
+                "chunk_spread": vals[e + 4]}
 
     def debug_stage(self, window, stage, v):
         """Stage 0: spread grid (n^d doubles); stage 1: adjoint NFFT S_k (complex M^d). Synchronous."""

@@ -815,8 +815,9 @@ int vec_ok(const Plan& p, const float* out, int64_t ld)
 // Work items: every non-empty cell's points in chunks of at most `chunk`, heaviest first within a
 // window; one device array holding the kernel kinds one after another (item_begin[k][s] absolute).
 // The chunk is the scheduling grain of the spread and gather kernels (addker_autotune chooses it).
-int build_items(Plan& p, int chunk)
+int build_items(Plan& p, int chunk, int chunk_sp)
 {
+    if (chunk_sp <= 0) chunk_sp = chunk;
     // two lists: the one every kernel uses, and the spread's, which differs for 2-D windows only
     std::vector<int4> lists[2][kKinds];
     for (int k = 0; k < kKinds; ++k) {
@@ -828,7 +829,7 @@ int build_items(Plan& p, int chunk)
             // spreading a 2-D window: few crowded cells whose 8x8 boxes overlap, so every item ends with
             // atomic adds to the same few hundred grid values; those items are kLowdChunkFactor times
             // larger (1-D windows, and the gathers, need the parallelism of small items more)
-            const int ch = (l == 1 && p.dims[s] == 2) ? chunk * kLowdChunkFactor : chunk;
+            const int ch = l == 0 ? chunk : (p.dims[s] == 2 ? chunk_sp * kLowdChunkFactor : chunk_sp);
             std::vector<int4> items;
             for (const int4& c : p.cells[s])
                 for (int st = 0; st < c.y; st += ch)
@@ -861,6 +862,7 @@ int build_items(Plan& p, int chunk)
     }
     if (!all.empty()) CK(cudaMemcpy(p.items, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice));
     p.chunk = chunk;
+    p.chunk_sp = chunk_sp;
     return ADDKER_OK;
 }
 
@@ -1240,7 +1242,7 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
     }
     for (int s = 0; s < P && status == ADDKER_OK; ++s) status = setup_window(p, s, points, keys, flag);
     if (keys) cudaFree(keys);
-    if (status == ADDKER_OK) status = build_items(p, kItemPoints);
+    if (status == ADDKER_OK) status = build_items(p, kItemPoints, kItemPoints);
     if (status == ADDKER_OK) status = dalloc(p, &p.wins_dev, P);
     if (status == ADDKER_OK) status = dalloc(p, &p.scale_dev, 3 * P);
     if (status == ADDKER_OK) status = dalloc(p, &p.dots, 2 * P);
@@ -1307,25 +1309,38 @@ int addker_autotune(addker_plan* plan, const float* v, int nrhs, int* chosen, do
     cudaEvent_t a = nullptr, b = nullptr;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    int status = ADDKER_OK, best = p.chunk;
+    int status = ADDKER_OK, best = p.chunk, best_sp = p.chunk_sp;
     double best_ms = 1e300;
-    for (int c = 0; c < nc && status == ADDKER_OK; ++c) {
-        CK(cudaStreamSynchronize(p.stream));
-        status = build_items(p, cand[c]);
+    // ms per product for the items cut by (chunk, chunk_sp); 0 on failure (status set)
+    auto time_items = [&](int chunk, int chunk_sp) -> double {
+        if (cudaStreamSynchronize(p.stream) != cudaSuccess) { status = ADDKER_ECUDA; return 0.0; }
+        status = build_items(p, chunk, chunk_sp);
         if (status == ADDKER_OK) status = product_all(p, v, nrhs, Kv, dK, -1, 0);       // warm-up
         cudaEventRecord(a, p.stream);
         for (int rep = 0; rep < 3 && status == ADDKER_OK; ++rep) status = product_all(p, v, nrhs, Kv, dK, -1, 0);
         cudaEventRecord(b, p.stream);
         float ms = 0.f;
-        if (status == ADDKER_OK && cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) {
-            if (times && c < cap) times[c] = ms / 3.0;
-            if (ms / 3.0 < best_ms) { best_ms = ms / 3.0; best = cand[c]; }
-        } else if (status == ADDKER_OK) {
-            status = ADDKER_ECUDA;
-        }
+        if (status == ADDKER_OK && cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess)
+            return ms / 3.0;
+        if (status == ADDKER_OK) status = ADDKER_ECUDA;
+        return 0.0;
+    };
+    // phase 1: one size for both lists; phase 2: the spread's size alone, the gather's kept
+    for (int c = 0; c < nc && status == ADDKER_OK; ++c) {
+        const double ms = time_items(cand[c], cand[c]);
+        if (status != ADDKER_OK) break;
+        if (times && c < cap) times[c] = ms;
+        if (ms < best_ms) { best_ms = ms; best = best_sp = cand[c]; }
+    }
+    const double joint_ms = best_ms;
+    for (int c = 0; c < nc && status == ADDKER_OK; ++c) {
+        const double ms = cand[c] == best ? joint_ms : time_items(best, cand[c]);
+        if (status != ADDKER_OK) break;
+        if (times && nc + c < cap) times[nc + c] = ms;
+        if (ms < best_ms) { best_ms = ms; best_sp = cand[c]; }
     }
     cudaStreamSynchronize(p.stream);
-    if (status == ADDKER_OK) status = build_items(p, best);
+    if (status == ADDKER_OK) status = build_items(p, best, best_sp);
     clear_graphs(p);
     p.graphs = graphs;
     p.prof = prof;
@@ -1677,6 +1692,7 @@ int addker_info(const addker_plan* plan, int64_t* info, int cap)
     v.push_back((int64_t)p.graph_cache.size());
     v.push_back(p.graph_replays);
     v.push_back(p.chunk);
+    v.push_back(p.chunk_sp);
     for (int i = 0; i < cap && i < (int)v.size(); ++i) info[i] = v[i];
     return (int)v.size();
 }

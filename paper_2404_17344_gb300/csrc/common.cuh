@@ -93,7 +93,8 @@ struct Plan {
     // window: items of window s are [item_begin[k][s], item_begin[k][s+1]) for its kind k = kind[s]
     int4* items = nullptr;
     int64_t items_cap = 0;
-    int chunk = kItemPoints;              // points per work item at most
+    int chunk = kItemPoints;              // points per work item at most (gathers)
+    int chunk_sp = kItemPoints;           // points per spread work item at most (x8 for 2-D windows)
     std::vector<std::vector<int4>> cells; // per window: non-empty cells (first point, count, packed cell, s)
     std::vector<int> item_begin[kKinds];
     std::vector<int> item_begin_sp[kKinds]; // the spread's list (larger items for 2-D windows), same array

@@ -193,8 +193,12 @@ def test_autotune_keeps_results(torch_cuda, cfg, N, nrhs):
     op = make_op(torch, wl)
     K0, D0 = op.matvec_all(V)
     chosen, times = op.autotune(V)
-    assert chosen in op.AUTOTUNE_CHUNKS and op.info()["chunk"] == chosen
-    assert all(t > 0 for t in times.values())
+    info = op.info()
+    assert chosen in op.AUTOTUNE_CHUNKS and info["chunk"] == chosen
+    assert info["chunk_spread"] in op.AUTOTUNE_CHUNKS
+    assert all(t > 0 for t in times.values()) and all(t > 0 for t in op.autotune_spread_times.values())
+    # the spread phase's entry for the joint winner repeats the joint timing
+    assert op.autotune_spread_times[chosen] == times[chosen]
     for _ in range(3):
         K1, D1 = op.matvec_all(V)
     assert rel(K1.cpu(), K0.cpu()) < TOL and rel(D1.cpu(), D0.cpu()) < TOL
