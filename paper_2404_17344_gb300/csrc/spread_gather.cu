@@ -263,7 +263,6 @@ template <bool WK, bool WD>
 __device__ __forceinline__ void gather3_item(const int4 it, const WinDev& P, float2* t, int lane, int r,
                                              const GatherArgs& g, const WinPoly& poly)
 {
-    constexpr int W = 8;
     float* __restrict__ outK = g.outK;
     float* __restrict__ outD = g.outD;
     const int64_t strideK = g.strideK, strideD = g.strideD, rstrideK = g.rstrideK, rstrideD = g.rstrideD;
