@@ -97,3 +97,19 @@ def test_es_vjp_is_refused(torch_cuda):
     with pytest.raises(native.AddkerError) as e:
         op.vjp(v, v)
     assert e.value.status == native.ADDKER_EINVAL
+
+
+@pytest.mark.parametrize("kernel,comp", [("matern", False), ("gauss", True), ("matern", True)])
+def test_es_window_with_other_options(torch_cuda, kernel, comp):
+    """The window choice composes with the kernel family and compensated accumulation: each combination
+    against the oracle with the same window and kernel."""
+    torch = torch_cuda
+    wl = workloads.make("c3", N=4000)
+    v = wl.vector()
+    op = make_op(torch, wl, kernel=kernel, compensated=comp)
+    Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
+    Kr, dKr = fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f, v.astype(np.float64), wl.bandwidth,
+                                 wl.cutoff, win="es", kernel=kernel)
+    assert rel(Kv.cpu(), Kr) < TOL
+    for s in range(wl.P):
+        assert rel(dK[s].cpu(), dKr[s]) < TOL, s
