@@ -252,6 +252,23 @@ def test_prescale_cube_matches_paper_rule(torch_cuda):
 
 
 @pytest.mark.slow
+def test_full_size_mixed_windows_sampled_rows(torch_cuda):
+    """N = 1e6, 15 features in windows of 3, 3, 3, 2, 2, 1, 1 (M = 32 / 16): every kernel kind at the
+    batched configuration's size, in one product, on 1024 sampled rows against the CPU NFFT (measured
+    at most 1.7e-6)."""
+    torch = torch_cuda
+    wl = workloads.make("c3", N=1_000_000)
+    v = wl.vector()
+    Kv, dK = make_op(torch, wl).matvec_all(torch.from_numpy(v).cuda())
+    Kv, dK = Kv.cpu().numpy(), dK.cpu().numpy()
+    rows = np.random.default_rng(1).choice(wl.N, 1024, replace=False)
+    Kn, dKn = oracle_all(wl, v, rows=rows)
+    assert rel(Kv[rows], Kn) < TOL
+    for s in range(wl.P):
+        assert rel(dK[s, rows], dKn[s]) < TOL, s
+
+
+@pytest.mark.slow
 def test_full_size_sampled_rows(torch_cuda):
     """N = 1e6, d = 9, three windows of 3 (the benchmark workload): GPU outputs on 1500 sampled rows
     against the CPU NFFT (all 1e6 points spread in FP64) and against the direct FP64 sums.
