@@ -123,3 +123,21 @@ def test_direct_fp64_gradient_on_a_subset(torch_cuda):
     assert rel(gv.cpu().numpy()[rows], dv[rows]) <= rel(nv[rows], dv[rows]) + TOL
     assert rel(gt.cpu().numpy()[:wl.P], dell) <= rel(nell, dell) + TOL
     assert rel(gx.cpu().numpy()[rows], dx) <= rel(nx[rows], dx) + TOL_X
+
+
+@pytest.mark.slow
+def test_vjp_at_the_configuration_size(torch_cuda):
+    """The differentiation configuration at its full size (N = 2e5, 12 features, 4 windows of 3): every
+    gradient against the oracle's FP64 NFFT gradients (the direct-sum comparison, O(N^2) in the oracle,
+    runs at N = 2e4 above)."""
+    torch = torch_cuda
+    wl = workloads.make("c2", N=200_000)
+    v, w = wl.vector(), wl.vector(which=2)
+    op = make_op(torch, wl)
+    gv, gt, gx = op.vjp(torch.from_numpy(v).cuda(), torch.from_numpy(w).cuda())
+    gv, gt, gx = gv.cpu().numpy(), gt.cpu().numpy(), gx.cpu().numpy()
+    rv, rell, rsf, rx = gradients.nfft_grad(wl.points, wl.windows, wl.ell, wl.sigma_f, v, w, wl.bandwidth, wl.cutoff)
+    assert rel(gv, rv) < TOL
+    assert rel(gt[:wl.P], rell) < TOL
+    assert abs(gt[wl.P] - rsf) <= TOL * abs(rsf)
+    assert rel(gx, rx) < TOL_X
