@@ -269,6 +269,22 @@ def test_full_size_mixed_windows_sampled_rows(torch_cuda):
 
 
 @pytest.mark.slow
+def test_gp_configuration_size_sampled_rows(torch_cuda):
+    """The GP configuration's operator at its full size (N = 2e6, 24 correlated features, 8 windows of 3):
+    the fused product on 512 sampled rows against the CPU NFFT (all 2e6 points spread in FP64)."""
+    torch = torch_cuda
+    wl = workloads.make("c4", N=2_000_000)
+    v = wl.vector()
+    Kv, dK = make_op(torch, wl).matvec_all(torch.from_numpy(v).cuda())
+    Kv, dK = Kv.cpu().numpy(), dK.cpu().numpy()
+    rows = np.random.default_rng(2).choice(wl.N, 512, replace=False)
+    Kn, dKn = oracle_all(wl, v, rows=rows)
+    assert rel(Kv[rows], Kn) < TOL
+    for s in range(wl.P):
+        assert rel(dK[s, rows], dKn[s]) < TOL, s
+
+
+@pytest.mark.slow
 def test_full_size_sampled_rows(torch_cuda):
     """N = 1e6, d = 9, three windows of 3 (the benchmark workload): GPU outputs on 1500 sampled rows
     against the CPU NFFT (all 1e6 points spread in FP64) and against the direct FP64 sums.
