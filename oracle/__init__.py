@@ -13,7 +13,9 @@ Derivatives" that it follows):
   fastsum.ndft_fastsum  exact trigonometric fast sum (eq. "approx fast sum")
   fastsum.nfft_fastsum  plain FP64 NFFT fast summation (adjoint NFFT, multiply, NFFT)
   fastsum.matvec_all    additive combination over windows, with the derivative scalings
-  kernels.*             kernels, regularisation, discrete Fourier coefficients
+  kernels.*             kernels, regularisation (radial, and the separable reading: tensor-product
+                        coefficients of 1-D least-squares Fourier extensions), discrete Fourier
+                        coefficients
   window.*              Kaiser-Bessel window and its Fourier transform
   bounds.*              the error bounds of Sec. 3.4 and the analytic coefficients
   gp.*                  regression system (CG), GP log marginal likelihood and its gradient,

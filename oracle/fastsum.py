@@ -162,9 +162,37 @@ KINDS = {"gauss": ("gauss", "der", 2.0), "matern": ("matern", "matern_der", 1.0)
 
 
 def window_coefficients(ell: float, d: int, M: int, p: int, eps_B: float, kernel: str = "gauss"):
+    """Coefficients of the kernel and its derivative kernel under the radial reading (degree p)."""
     kk, kd, _ = KINDS[kernel]
     return (kernels.coefficients(ell, d, M, p, eps_B, kk),
             kernels.coefficients(ell, d, M, p, eps_B, kd))
+
+
+def default_reg(kernel: str) -> str:
+    """The separable reading for the Gaussian family, the radial one for Matern(1/2) (not separable)."""
+    return "separable" if kernel == "gauss" else "radial"
+
+
+def coefficients_for(xs: np.ndarray, ell: float, M: int, p=None, eps_B: float = 1.0 / 16.0,
+                     kernel: str = "gauss", reg: str | None = None):
+    """(c_hat, c_hat^der) of one window whose source points (N x d_s, the window's coordinates) are xs.
+
+    reg 'separable' (default for the Gaussian): kernels.coefficients_separable on the fit intervals
+    a_t of every axis, computed from the largest |coordinate| of xs; reg 'radial': the radial
+    regularisation of degree p (kernels.default_p when None)."""
+    reg = default_reg(kernel) if reg is None else reg
+    d = xs.shape[1]
+    if reg == "separable":
+        if kernel != "gauss":
+            raise ValueError("the separable reading covers the Gaussian family only")
+        maxabs = np.abs(xs).max(axis=0) if xs.shape[0] else np.zeros(d)
+        iv = [kernels.fit_interval(float(a), M, eps_B) for a in maxabs]
+        return (kernels.coefficients_separable(ell, M, iv, "gauss"),
+                kernels.coefficients_separable(ell, M, iv, "der"))
+    if reg != "radial":
+        raise ValueError(reg)
+    ps = kernels.default_p(M, eps_B) if p is None else int(p)
+    return window_coefficients(ell, d, M, ps, eps_B, kernel)
 
 
 def direct_matern(points, windows, ell, sigma_f: float, v, rows=None, block: int = 256):
@@ -190,11 +218,13 @@ def direct_matern(points, windows, ell, sigma_f: float, v, rows=None, block: int
 
 def matvec_all(points, windows, ell, sigma_f: float, v, bandwidth, cutoff: int, p=None,
                eps_B: float = 1.0 / 16.0, sigma: float = 2.0, level: str = "nfft", rows=None,
-               kernel: str = "gauss", win: str = "kb"):
+               kernel: str = "gauss", win: str = "kb", reg: str | None = None, coefs=None):
     """Fused product: returns (K v, dK/d ell [P, .]) at level 'nfft' (CPU NFFT fast sum)
     or 'ndft' (exact trigonometric sum). v is one right-hand side of length N. With `rows`, the
     outputs are evaluated only at those points (all N points are still sources). `win` selects the
-    NFFT window ('kb' Kaiser-Bessel, 'es' exponential of semicircle)."""
+    NFFT window ('kb' Kaiser-Bessel, 'es' exponential of semicircle); `reg` the reading of the
+    regularisation (coefficients_for). `coefs` may hold the P pairs (c_hat, c_hat^der) from an earlier
+    call (they depend only on the points' extents and the hyperparameters)."""
     X = np.asarray(points, dtype=np.float32).astype(np.float64)
     v = np.asarray(v, dtype=np.float64)
     P = len(windows)
@@ -207,9 +237,11 @@ def matvec_all(points, windows, ell, sigma_f: float, v, bandwidth, cutoff: int, 
     for s, w in enumerate(windows):
         d = len(w)
         M = int(bandwidth[s])
-        ps = kernels.default_p(M, eps_B) if p is None else int(p)
-        cg, cd = window_coefficients(float(ell[s]), d, M, ps, eps_B, kernel)
         xs = np.ascontiguousarray(X[:, list(w)])
+        if coefs is not None:
+            cg, cd = coefs[s]
+        else:
+            cg, cd = coefficients_for(xs, float(ell[s]), M, p, eps_B, kernel, reg)
         xt = None if rows is None else np.ascontiguousarray(T[:, list(w)])
         if level == "nfft":
             outK, outD = nfft_fastsum(xs, v, [cg, cd], int(round(sigma * M)), cutoff, sigma, targets=xt, win=win)

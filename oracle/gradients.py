@@ -18,7 +18,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import _clib, fastsum, kernels, window
+from . import _clib, fastsum, window
 
 
 def direct_grad(points, windows, ell, sigma_f, v, w, rows=None):
@@ -61,8 +61,11 @@ def gather_grad(x, h, n, m, sigma=2.0):
     return val, grad
 
 
-def nfft_grad(points, windows, ell, sigma_f, v, w, bandwidth, cutoff, p=None, eps_B=1.0 / 16.0, sigma=2.0):
-    """Returns (grad_v, grad_ell[P], grad_sigma_f, grad_x[N, d]) of f~ = w^T K~ v."""
+def nfft_grad(points, windows, ell, sigma_f, v, w, bandwidth, cutoff, p=None, eps_B=1.0 / 16.0, sigma=2.0,
+              reg=None):
+    """Returns (grad_v, grad_ell[P], grad_sigma_f, grad_x[N, d]) of f~ = w^T K~ v. The coefficients
+    (fastsum.coefficients_for) are held fixed in the coordinate gradient: under the separable reading
+    their fit intervals are set-up constants of the operator, like the grid and the window."""
     X = np.asarray(points, dtype=np.float32).astype(np.float64)
     N, d = X.shape
     v = np.asarray(v, dtype=np.float64)
@@ -70,15 +73,16 @@ def nfft_grad(points, windows, ell, sigma_f, v, w, bandwidth, cutoff, p=None, ep
     P = len(windows)
     if np.isscalar(bandwidth):
         bandwidth = [int(bandwidth)] * P
-    Kw, dKw = fastsum.matvec_all(points, windows, ell, sigma_f, w, bandwidth, cutoff, p=p, eps_B=eps_B, sigma=sigma)
-    Kv, _ = fastsum.matvec_all(points, windows, ell, sigma_f, v, bandwidth, cutoff, p=p, eps_B=eps_B, sigma=sigma)
+    Kw, dKw = fastsum.matvec_all(points, windows, ell, sigma_f, w, bandwidth, cutoff, p=p, eps_B=eps_B, sigma=sigma,
+                                 reg=reg)
+    Kv, _ = fastsum.matvec_all(points, windows, ell, sigma_f, v, bandwidth, cutoff, p=p, eps_B=eps_B, sigma=sigma,
+                               reg=reg)
     gx = np.zeros((N, d))
     for s, win in enumerate(windows):
         M = int(bandwidth[s])
-        ps = kernels.default_p(M, eps_B) if p is None else int(p)
-        cg = kernels.coefficients(float(ell[s]), len(win), M, ps, eps_B)
         n = int(round(sigma * M))
         xs = np.ascontiguousarray(X[:, list(win)])
+        cg, _ = fastsum.coefficients_for(xs, float(ell[s]), M, p, eps_B, "gauss", reg)
         _, gv = gather_grad(xs, _grid(xs, v, cg, n, cutoff, sigma), n, cutoff, sigma)
         _, gw = gather_grad(xs, _grid(xs, w, cg, n, cutoff, sigma), n, cutoff, sigma)
         gx[:, list(win)] += sigma_f ** 2 * (w[:, None] * gv + v[:, None] * gw)

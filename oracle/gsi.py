@@ -20,15 +20,13 @@ import itertools
 
 import numpy as np
 
-from . import fastsum, kernels
+from . import fastsum
 
 
-def window_spectrum(points, window, ell: float, v, M: int, p=None, eps_B: float = 1.0 / 16.0):
+def window_spectrum(points, window, ell: float, v, M: int, p=None, eps_B: float = 1.0 / 16.0, reg=None):
     """c_hat_k S(k, W) for k in I_M^d (array indexed k + M/2), S by the exact trigonometric sum."""
     x = np.asarray(points, dtype=np.float32).astype(np.float64)[:, list(window)]
-    d = len(window)
-    ps = kernels.default_p(M, eps_B) if p is None else int(p)
-    chat = kernels.coefficients(float(ell), d, M, ps, eps_B, "gauss")
+    chat, _ = fastsum.coefficients_for(x, float(ell), M, p, eps_B, "gauss", reg)
     S = fastsum.adjoint_exact(x, np.asarray(v, dtype=np.float64), M)
     return chat * S
 
@@ -43,7 +41,7 @@ def support_pattern(M: int, d: int) -> np.ndarray:
     return pat
 
 
-def gsi(points, windows, ell, v, bandwidth, p=None, eps_B: float = 1.0 / 16.0):
+def gsi(points, windows, ell, v, bandwidth, p=None, eps_B: float = 1.0 / 16.0, reg=None):
     """Returns (rho, theta, total): dicts keyed by feature subsets (sorted tuples), rho_u = theta_u / total."""
     P = len(windows)
     if np.isscalar(bandwidth):
@@ -51,7 +49,7 @@ def gsi(points, windows, ell, v, bandwidth, p=None, eps_B: float = 1.0 / 16.0):
     theta = {}
     for s, w in enumerate(windows):
         M = int(bandwidth[s])
-        spec = window_spectrum(points, w, ell[s], v, M, p, eps_B)
+        spec = window_spectrum(points, w, ell[s], v, M, p, eps_B, reg)
         pat = support_pattern(M, len(w))
         e = np.abs(spec) ** 2
         for b in range(1, 2 ** len(w)):

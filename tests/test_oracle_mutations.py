@@ -64,3 +64,38 @@ def test_window_transform_mismatch_is_caught(monkeypatch):
     real = window.phihat_quadrature
     monkeypatch.setattr(window, "phihat_quadrature", lambda k, n, m, sigma=2.0, **kw: real(k, n, m, 1.5, **kw))
     assert _adjoint_err(x, v, 32) > 1e-3
+
+
+def test_unhalved_extension_coefficients_are_caught(monkeypatch):
+    """Forgetting to split b_k between c_{+k} and c_{-k} doubles every non-constant term: the exact
+    reproduction of a cosine polynomial fails."""
+    M, a = 16, 0.3
+    f = lambda x: 0.3 + 0.5 * np.cos(2 * np.pi * 3 * x)
+    x = kernels.extension_nodes(a, M)
+    good = kernels.cosine_extension(f(x), a, M)
+    assert abs(good[M // 2 + 3] - 0.25) < 1e-9
+    real = kernels.cosine_extension
+
+    def bad(values, a, M):
+        c = real(values, a, M)
+        c[np.arange(M) != M // 2] *= 2
+        return c
+    monkeypatch.setattr(kernels, "cosine_extension", bad)
+    worse = kernels.cosine_extension(f(x), a, M)
+    assert abs(worse[M // 2 + 3] - 0.25) > 0.1
+
+
+def test_dropped_term_of_the_derivative_sum_is_caught():
+    """The derivative kernel's coefficients are a d-term sum (Sec. 3.4); dropping the last term breaks
+    the agreement with kappa_der on the coordinate box."""
+    M, ell, iv = 16, 0.5, [0.3, 0.3, 0.3]
+    rng = np.random.default_rng(8)
+    r = rng.uniform(-0.3, 0.3, (500, 3))
+    want = kernels.kappa(np.linalg.norm(r, axis=1), ell, "der")
+    good = kernels.coefficients_separable(ell, M, iv, "der")
+    assert np.abs(kernels.trig_poly_eval(good, r) - want).max() < 1e-4
+    f = [kernels.factor_coefficients(ell, a, M, "gauss") for a in iv]
+    g = [kernels.factor_coefficients(ell, a, M, "der") for a in iv]
+    o = np.multiply.outer
+    two_terms = o(o(g[0], f[1]), f[2]) + o(o(f[0], g[1]), f[2])
+    assert np.abs(kernels.trig_poly_eval(two_terms, r) - want).max() > 1e-2

@@ -124,13 +124,13 @@ def test_end_to_end_c0_levels():
 
 
 def test_large_ell_and_fine_grid_converge_to_direct():
-    """With a wide kernel (ell = 3) the periodisation is nearly smooth and the fast sum meets the
-    direct sum closely; M = 64 is more accurate than M = 32."""
+    """With a wide kernel (ell = 3) the radially regularised periodisation is nearly smooth and the fast
+    sum meets the direct sum closely; M = 64 is more accurate than M = 32."""
     wl = workloads.make("c0", N=500)
     v = wl.vector().astype(np.float64)
     Kd, _ = fastsum.direct(wl.points, wl.windows, [3.0], 1.0, v)
-    K32, _ = fastsum.matvec_all(wl.points, wl.windows, [3.0], 1.0, v, 32, 4)
-    K64, _ = fastsum.matvec_all(wl.points, wl.windows, [3.0], 1.0, v, 64, 4)
+    K32, _ = fastsum.matvec_all(wl.points, wl.windows, [3.0], 1.0, v, 32, 4, reg="radial")
+    K64, _ = fastsum.matvec_all(wl.points, wl.windows, [3.0], 1.0, v, 64, 4, reg="radial")
     assert rel(K64, Kd) < rel(K32, Kd) < 1e-4
 
 
@@ -144,8 +144,9 @@ def test_sigma_f_and_derivative_scalings():
     np.testing.assert_allclose(D2, 6.25 * D1, rtol=1e-13)
     X = wl.points.astype(np.float64)
     for s, w in enumerate(wl.windows):
-        cd = kernels.coefficients(wl.ell[s], 3, 16, kernels.default_p(16, 1 / 16), 1 / 16, "der")
-        raw = fastsum.nfft_fastsum(np.ascontiguousarray(X[:, list(w)]), v, [cd], 32, 4)[0]
+        xs = np.ascontiguousarray(X[:, list(w)])
+        _, cd = fastsum.coefficients_for(xs, wl.ell[s], 16)
+        raw = fastsum.nfft_fastsum(xs, v, [cd], 32, 4)[0]
         np.testing.assert_allclose(D1[s], 2.0 / wl.ell[s] * raw, rtol=1e-13)
 
 
