@@ -95,6 +95,26 @@ extern "C" {
 #define ADDKER_KERNEL_GAUSS 0
 #define ADDKER_KERNEL_MATERN12 1
 
+/* How the non-periodic kernel becomes a trigonometric polynomial (addker_opts.reg). The paper smooths
+ * the periodisation near the boundary of the period (Sec. 3.1, after Potts and Steidl) without writing
+ * the construction down; two readings are built:
+ *   ADDKER_REG_SEPARABLE  (default for the Gaussian) Sec. 3.4's tensor-product form: the Gaussian's
+ *                         coefficients c_k = prod_t c_{k_t}(f), the derivative kernel's the d_s-term sum
+ *                         sum_t c_{k_t}(g) prod_{u != t} c_{k_u}(f), f(x) = exp(-x^2/(2 ell^2)),
+ *                         g(x) = (x^2/(2 ell^2)) f(x); each 1-D factor is the least-squares Fourier
+ *                         extension (cosines of degree < M/2, FP64 Householder QR on 4M equispaced nodes)
+ *                         of f or g on [0, a_t], a_t = min(1/2 - eps_B, max(max(1/4, 1/2 - 4/M),
+ *                         2 max_j |x_{j,t}|)): the interval that holds every coordinate difference of
+ *                         axis t. Gaussian family only.
+ *   ADDKER_REG_RADIAL     the radial profile kept up to a = 1/2 - eps_B, joined to the constant kappa(1/2)
+ *                         by the degree 2p-1 two-point Hermite polynomial (opts.p), sampled on the M^d
+ *                         grid and transformed (Lemma "aliasing error"). The only choice for Matern(1/2).
+ * At M = 32 on the nine-feature benchmark's windows the derivative products against the direct sums are
+ * below 1e-5 with the separable reading and 3.6e-4 .. 2.8e-3 with the radial one. */
+#define ADDKER_REG_DEFAULT (-1)
+#define ADDKER_REG_SEPARABLE 0
+#define ADDKER_REG_RADIAL 1
+
 typedef struct addker_plan addker_plan;
 
 /* Optional settings; pass NULL to addker_setup for the defaults. */
@@ -102,13 +122,16 @@ typedef struct {
     double sigma_os;     /* oversampling factor sigma; grid n = sigma * M per dimension (default 2.0) */
     double eps_B;        /* boundary width eps_B of the regularisation (default 1/16); points must satisfy
                             ||x^{W_s}|| <= 1/4 - eps_B/2 */
-    int    p;            /* regularisation degree (transition polynomial of degree 2p-1); -1 = default
-                            max(1, floor(M eps_B + 1/2)); 0 = no regularisation (plain periodic continuation) */
+    int    p;            /* radial reading only: regularisation degree (transition polynomial of degree 2p-1);
+                            -1 = default max(1, floor(M eps_B + 1/2)); 0 = no regularisation (plain periodic
+                            continuation) */
     int    window;       /* ADDKER_WIN_KB (default) or ADDKER_WIN_ES */
     int    kernel;       /* ADDKER_KERNEL_GAUSS (default) or ADDKER_KERNEL_MATERN12 */
     int    compensated;  /* 1: compensated grid accumulation: the spread's FP32 tile sums are added into an
                             FP64 grid (no rounding error from the order of the atomic adds), which the
                             forward transform rounds once to FP32; 0 (default): plain FP32 adds */
+    int    reg;          /* ADDKER_REG_DEFAULT (separable for the Gaussian, radial for Matern(1/2)),
+                            ADDKER_REG_SEPARABLE (Gaussian only) or ADDKER_REG_RADIAL */
     void*  stream;       /* cudaStream_t for every product of this plan; NULL = legacy default stream */
 } addker_opts;
 
@@ -135,8 +158,11 @@ int addker_opts_default(addker_opts* opts);
  *              (so no support wraps around the grid)
  *   opts       host or NULL
  *
- * Errors: ADDKER_EINVAL for bad sizes/layout, ADDKER_EDOMAIN for a point outside
- * the ball (checked on the device), ADDKER_ENOMEM, ADDKER_ECUDA. Synchronises the
+ * Under the separable reading the coefficients also depend on the points' largest |coordinate| per
+ * feature (the fit intervals), taken here and kept for addker_set_params.
+ *
+ * Errors: ADDKER_EINVAL for bad sizes/layout (or the separable reading with Matern(1/2)), ADDKER_EDOMAIN
+ * for a point outside the ball (checked on the device), ADDKER_ENOMEM, ADDKER_ECUDA. Synchronises the
  * plan's stream before returning.
  */
 int addker_setup(addker_plan** plan, const float* points, int64_t N, int d,
@@ -367,17 +393,17 @@ int addker_debug_stage(addker_plan* plan, int window, int stage, const float* v,
 
 /*
  * The fused product for ONE window without any device allocation. The paper has no counterpart;
- * this entry point exists for callers that cannot call cudaMalloc: code that runs while a stream is
- * being captured into a CUDA graph (allocation is not a capturable operation), servers and real-time
- * loops that forbid device allocation after start-up so their memory use stays fixed, and hosts whose
- * own allocator owns the device memory. Every working buffer (grids, transform buffers, multipliers,
- * twiddles, the FP64 coefficient work area) lives in one fixed 9 MiB array in device memory that the
- * library declares; every GPU that loads the library keeps it until the process exits.
+ * this entry point exists for callers that cannot call cudaMalloc: servers and real-time loops that
+ * forbid device allocation after start-up so that their memory use stays fixed, and hosts whose own
+ * allocator owns the device memory. Every working buffer (grids, transform buffers, multipliers,
+ * twiddles, the FP64 coefficient work area, the points' coordinate range) lives in one fixed 9 MiB
+ * array in device memory that the library declares; every GPU that loads the library keeps it until the
+ * process exits.
  *
  *   points   device, N x d float32 row-major: all d features form the window (1 <= d <= 3), each point
  *            inside the ball ||x|| <= 1/4 - eps_B/2 with eps_B = 1/16
  *   ell, sigma_f, bandwidth (M), cutoff (m): as in addker_setup, with oversampling 2, eps_B = 1/16 and
- *            the default regularisation degree
+ *            the Gaussian's default reading (ADDKER_REG_SEPARABLE)
  *   v        device, N floats;  Kv, dKdell: device, N floats each (dKdell may be NULL)
  *            Kv = sigma_f^2 K v,  dKdell = sigma_f^2 (2/ell) K^der v
  *   stream   cudaStream_t (NULL = legacy default); the call waits for it before returning
@@ -385,10 +411,9 @@ int addker_debug_stage(addker_plan* plan, int window, int stage, const float* v,
  * Limit: bandwidth M <= 32 (grid n = 64), d <= 3, any N (points are not sorted, so nothing grows with
  * N). Larger requests return ADDKER_ELIMIT; malformed ones ADDKER_EINVAL; a point outside the ball or
  * not finite gives ADDKER_EDOMAIN (outputs then undefined). The first call on a device looks up the
- * array's device address (once per device, with that device current); make that first call before
- * any stream capture. All calls share the one array and it keeps the last call's contents (each call
- * clears what must start at zero): calls that overlap on the GPU, on any stream or thread, race.
- * No cudaMalloc, cudaFree or other allocating routine is called.
+ * array's device address (once per device, with that device current). All calls share the one array and
+ * it keeps the last call's contents (each call clears what must start at zero): calls that overlap on
+ * the GPU, on any stream or thread, race. No cudaMalloc, cudaFree or other allocating routine is called.
  */
 int addker_fastsum_noalloc(const float* points, int64_t N, int d, double ell, double sigma_f,
                            int bandwidth, int cutoff, const float* v, float* Kv, float* dKdell,

@@ -47,6 +47,8 @@ def lib():
             L.orc_gather_grad.restype = None
             L.orc_num_threads.argtypes = []
             L.orc_num_threads.restype = i32
+            L.orc_set_threads.argtypes = [i32]
+            L.orc_set_threads.restype = None
             _lib = L
     return _lib
 

@@ -28,6 +28,8 @@ Additive kernel (Sec. 1 eq. "wind_gauss_anova_kernel", Sec. 3.3):
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
 
 from . import _clib
@@ -107,7 +109,10 @@ def ndft_fastsum(x: np.ndarray, v: np.ndarray, chats) -> list:
     return [forward_exact(x, c * S).real for c in chats]
 
 
+@functools.lru_cache(maxsize=64)
 def _phihat_grid(M: int, n: int, m: int, sigma: float, d: int, win: str = "kb") -> np.ndarray:
+    """prod_t phi_hat(k_t) on I_M^d (the window transform depends only on the settings: computed once
+    per setting and kept, like the setup of a plan; callers do not modify it)."""
     ph = window.phihat_quadrature(np.arange(-M // 2, M // 2), n, m, sigma, window=win)
     out = ph
     for _ in range(d - 1):

@@ -63,6 +63,16 @@ static double window_value(double t, int m, double shape, int kind)
     return kind == 1 ? es(t, m, shape) : kb(t, m, shape);
 }
 
+/* Threads of the OpenMP loops below (timing the baseline on one core or on all of them). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

@@ -51,13 +51,17 @@ class AddKer:
     windows: list of feature-index tuples (1 to 3 features each).
     ell: per-window length scales; sigma_f: signal standard deviation.
     bandwidth: M (int or per-window list), cutoff: window cutoff m.
+    reg: the reading of the regularisation, None (the default: 'separable' for the Gaussian, 'radial'
+    for Matern(1/2)), 'separable' or 'radial' (degree p).
     """
 
     KERNELS = {"gauss": native.ADDKER_KERNEL_GAUSS, "matern": native.ADDKER_KERNEL_MATERN12}
     WINDOWS = {"kb": native.ADDKER_WIN_KB, "es": native.ADDKER_WIN_ES}
+    REGS = {None: native.ADDKER_REG_DEFAULT, "separable": native.ADDKER_REG_SEPARABLE,
+            "radial": native.ADDKER_REG_RADIAL}
 
     def __init__(self, points, windows, ell, sigma_f=1.0, bandwidth=32, cutoff=4, eps_B=1.0 / 16.0,
-                 p=-1, sigma_os=2.0, kernel="gauss", compensated=False, window="kb"):
+                 p=-1, sigma_os=2.0, kernel="gauss", compensated=False, window="kb", reg=None):
         L = native.lib()
         pts = _dev_f32(points, "points")
         if pts.dim() != 2:
@@ -81,6 +85,9 @@ class AddKer:
             raise ValueError(f"window must be one of {sorted(self.WINDOWS)}")
         opts.window = self.WINDOWS[window]
         opts.compensated = 1 if compensated else 0
+        if reg not in self.REGS:
+            raise ValueError("reg must be None, 'separable' or 'radial'")
+        opts.reg = self.REGS[reg]
         opts.stream = _stream_ptr()
         plan = ctypes.c_void_p()
         native.check(L.addker_setup(ctypes.byref(plan), ctypes.c_void_p(pts.data_ptr()), self.N, self.d, off, feat,

@@ -195,6 +195,133 @@ __global__ void k_coef_sample(int M, double ell, Transition tr, double* __restri
     }
 }
 
+// ------------------------------------------- separable coefficients (FP64), Sec. 3.4 ----
+// The Gaussian's coefficients are a tensor product over the window's axes, c_k = prod_t c_{k_t}(f), and
+// the derivative kernel's the D-term sum sum_t c_{k_t}(g) prod_{u != t} c_{k_u}(f), f(x) = exp(-x^2/(2 ell^2)),
+// g(x) = (x^2/(2 ell^2)) f(x). Each 1-D factor is the least-squares Fourier extension of f (or g) on the
+// interval [0, a_t] that holds every coordinate difference of axis t:
+//   a_t = min(1/2 - eps_B, max(max(1/4, 1/2 - 4/M), 2 max_j |x_{j,t}|)),
+// fitted on J = 4M equispaced nodes a_t i/(J-1) by cos(2 pi k x), k < K = M/2. The floor keeps the
+// basis well conditioned (condition number below ~1e5); the fit is already within 1e-8 there.
+
+// One block per axis t: Householder QR of the J x K cosine matrix with the two right-hand sides f, g
+// appended (J x (K+2), column-major in dynamic shared memory), then back substitution.
+// range: per-feature [min, max] of the points (2 floats per feature); feat[t]: the axis's feature.
+// out[(2t + q) K + k] = b_k of f (q = 0) or g (q = 1).
+__global__ void k_fit_extension(int M, double ell, double eps_B, const float* __restrict__ range, int f0, int f1,
+                                int f2, double* __restrict__ out)
+{
+    extern __shared__ double A[];
+    __shared__ double red[32];
+    __shared__ double s_beta, s_alpha;
+    const int t = blockIdx.x;
+    const int f = t == 0 ? f0 : (t == 1 ? f1 : f2);
+    const int J = 4 * M, K = M / 2, C = K + 2;
+    const double maxabs = fmax(-(double)range[2 * f], (double)range[2 * f + 1]);
+    const double a = fmin(0.5 - eps_B, fmax(fmax(0.25, 0.5 - 4.0 / M), 2.0 * maxabs));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int i = tid; i < J; i += blockDim.x) {
+        const double x = a * i / (J - 1);
+        for (int k = 0; k < K; ++k) A[k * J + i] = cospi(2.0 * k * x);
+        const double q = x * x / (2.0 * ell * ell), e = exp(-q);
+        A[K * J + i] = e;
+        A[(K + 1) * J + i] = q * e;
+    }
+    __syncthreads();
+    for (int c = 0; c < K; ++c) {
+        double ss = 0.0;
+        for (int i = c + tid; i < J; i += blockDim.x) ss += A[c * J + i] * A[c * J + i];
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0) red[warp] = ss;
+        __syncthreads();
+        if (tid == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < nwarps; ++w) tot += red[w];
+            const double x0 = A[c * J + c];
+            const double alpha = x0 >= 0.0 ? -sqrt(tot) : sqrt(tot);
+            const double v0 = x0 - alpha;                  // no cancellation: alpha has x0's opposite sign
+            const double vv = tot - x0 * x0 + v0 * v0;
+            s_beta = vv > 0.0 ? 2.0 / vv : 0.0;
+            s_alpha = alpha;
+            A[c * J + c] = v0;                             // the reflector v = (v0, A[c+1.., c])
+        }
+        __syncthreads();
+        for (int j = c + 1 + warp; j < C; j += nwarps) {   // apply I - beta v v^T to the later columns
+            double dt = 0.0;
+            for (int i = c + lane; i < J; i += 32) dt += A[c * J + i] * A[j * J + i];
+            for (int o = 16; o > 0; o >>= 1) dt += __shfl_xor_sync(0xffffffffu, dt, o);
+            const double sc = s_beta * dt;
+            for (int i = c + lane; i < J; i += 32) A[j * J + i] -= sc * A[c * J + i];
+        }
+        __syncthreads();
+        if (tid == 0) A[c * J + c] = s_alpha;              // R's diagonal
+        __syncthreads();
+    }
+    if (tid < 2) {                                         // R b = (Q^T rhs)[0..K), R[k][j] = A[j J + k]
+        double x[kMaxBandwidth / 2];
+        for (int k = K - 1; k >= 0; --k) {
+            double acc = A[(K + tid) * J + k];
+            for (int j = k + 1; j < K; ++j) acc -= A[j * J + k] * x[j];
+            x[k] = acc / A[k * J + k];
+        }
+        for (int k = 0; k < K; ++k) out[(2 * t + tid) * K + k] = x[k];
+    }
+}
+
+// c_hat and c_hat^der on I_M^D (layout [k_0]..[k_{D-1}], last fastest) from the fitted factors:
+// c_{k}(.) = b_0 at k = 0, b_|k| / 2 for 0 < |k| < M/2, 0 at k = -M/2.
+template <int D>
+__global__ void k_coef_tensor(int M, const double* __restrict__ fit, double* __restrict__ outK,
+                              double* __restrict__ outD)
+{
+    int64_t total = 1;
+    for (int t = 0; t < D; ++t) total *= M;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int K = M / 2;
+    double fv[3], gv[3];
+    int64_t rem = idx;
+    for (int t = D - 1; t >= 0; --t) {
+        const int k = (int)(rem % M) - K;
+        rem /= M;
+        const int ak = k < 0 ? -k : k;
+        const double* bf = fit + (2 * t) * K;
+        const double* bg = fit + (2 * t + 1) * K;
+        if (ak >= K) { fv[t] = 0.0; gv[t] = 0.0; }
+        else if (ak == 0) { fv[t] = bf[0]; gv[t] = bg[0]; }
+        else { fv[t] = 0.5 * bf[ak]; gv[t] = 0.5 * bg[ak]; }
+    }
+    double cK = 1.0, cD = 0.0;
+    for (int t = 0; t < D; ++t) {
+        double term = gv[t];
+        for (int u = 0; u < D; ++u) if (u != t) term *= fv[u];
+        cD += term;
+        cK *= fv[t];
+    }
+    outK[idx] = cK;
+    outD[idx] = cD;
+}
+
+// Enqueue the separable coefficients of one window (D axes, features feat[0..D)) into cK, cD (M^D
+// doubles each), using fit (2 D K doubles) for the 1-D factors.
+cudaError_t separable_coefficients(int D, int M, double ell, double eps_B, const float* range, const int* feat,
+                                   double* fit, double* cK, double* cD, cudaStream_t st)
+{
+    const int J = 4 * M, K = M / 2;
+    const size_t shm = sizeof(double) * (size_t)J * (K + 2);
+    cudaError_t e = cudaFuncSetAttribute(k_fit_extension, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (e != cudaSuccess) return e;
+    k_fit_extension<<<D, 128, shm, st>>>(M, ell, eps_B, range, feat[0], D > 1 ? feat[1] : 0, D > 2 ? feat[2] : 0,
+                                         fit);
+    int64_t total = 1;
+    for (int t = 0; t < D; ++t) total *= M;
+    const int th = 256, bl = (int)((total + th - 1) / th);
+    if (D == 1) k_coef_tensor<1><<<bl, th, 0, st>>>(M, fit, cK, cD);
+    else if (D == 2) k_coef_tensor<2><<<bl, th, 0, st>>>(M, fit, cK, cD);
+    else k_coef_tensor<3><<<bl, th, 0, st>>>(M, fit, cK, cD);
+    return cudaGetLastError();
+}
+
 // out[a][k][b] = (1/M) sum_j in[a][j][b] cos(2 pi (j - M/2)(k - M/2) / M); the sine part of the DFT
 // vanishes for even, real samples.
 __global__ void k_coef_dft(const double* __restrict__ in, double* __restrict__ out, int A, int M, int B)
@@ -356,6 +483,16 @@ __global__ void k_feature_range(const float* __restrict__ X, int64_t N, int d, f
         atomic_max_float(mm + 2 * f + 1, hi);
         if (nonfinite) atomicOr(bad, 1);
     }
+}
+
+// range[2f] = +inf, range[2f + 1] = -inf for f < d, *bad = 0: the start of k_feature_range.
+__global__ void k_range_init(float* __restrict__ range, int d, int* __restrict__ bad)
+{
+    for (int f = threadIdx.x; f < d; f += blockDim.x) {
+        range[2 * f] = __int_as_float(0x7f800000);
+        range[2 * f + 1] = -__int_as_float(0x7f800000);
+    }
+    if (threadIdx.x == 0) *bad = 0;
 }
 
 // Y[j][f] = X[j][f] * scale[f] + shift[f]
@@ -602,36 +739,52 @@ void window_transform(const WinPoly& poly, int m, int n, int M, double* out)
 int compute_multipliers(Plan& p, int s)
 {
     WinDev& w = p.win[s];
-    // default degree: M eps_B rounded half up, at least 1
-    int ps = p.p_opt >= 0 ? p.p_opt : std::max(1, (int)std::floor(w.M * p.eps_B + 0.5));
-    Transition tr;
-    CS(make_transition(p.ell[s], ps, p.eps_B, p.kernel, &tr));
     int64_t total = 1;
     for (int t = 0; t < w.D; ++t) total *= w.M;
-    double *a = nullptr, *b = nullptr, *c = nullptr, *d = nullptr, *ph = nullptr;
-    CK(cudaMalloc(&a, sizeof(double) * (total * 4 + w.M)));
+    double *a = nullptr, *b = nullptr, *c = nullptr, *d = nullptr, *ph = nullptr, *fit = nullptr;
+    CK(cudaMalloc(&a, sizeof(double) * (total * 4 + 4 * w.M)));
     b = a + total;
     c = b + total;
     d = c + total;
     ph = d + total;
+    fit = ph + w.M;                                   // 2 D (M/2) <= 3 M doubles
     std::vector<double> phat(w.M);
     window_transform(p.poly, w.m, w.n, w.M, phat.data());
-    CK(cudaMemcpy(ph, phat.data(), sizeof(double) * w.M, cudaMemcpyHostToDevice));
     cudaStream_t st = p.stream;
     int th = 256, bl = grid_blocks(total, th);
-    if (w.D == 1) k_coef_sample<1><<<bl, th, 0, st>>>(w.M, p.ell[s], tr, a, b);
-    else if (w.D == 2) k_coef_sample<2><<<bl, th, 0, st>>>(w.M, p.ell[s], tr, a, b);
-    else k_coef_sample<3><<<bl, th, 0, st>>>(w.M, p.ell[s], tr, a, b);
-    // separable DFT along each axis (in place via ping-pong): layout [k0]..[k_{D-1}], last fastest
     double* src[2] = {a, b};
-    double* dst[2] = {c, d};
-    for (int t = 0; t < w.D; ++t) {
-        int64_t B = 1, A = 1;
-        for (int u = t + 1; u < w.D; ++u) B *= w.M;
-        for (int u = 0; u < t; ++u) A *= w.M;
-        for (int q = 0; q < 2; ++q) {
-            k_coef_dft<<<bl, th, 0, st>>>(src[q], dst[q], (int)A, w.M, (int)B);
-            std::swap(src[q], dst[q]);
+    if (cudaMemcpy(ph, phat.data(), sizeof(double) * w.M, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(a);
+        return ADDKER_ECUDA;
+    }
+    if (p.reg == ADDKER_REG_SEPARABLE) {
+        if (separable_coefficients(w.D, w.M, p.ell[s], p.eps_B, p.range, w.feat, fit, a, b, st) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(a);
+            return ADDKER_ECUDA;
+        }
+    } else {
+        // radial reading: default degree M eps_B rounded half up, at least 1
+        int ps = p.p_opt >= 0 ? p.p_opt : std::max(1, (int)std::floor(w.M * p.eps_B + 0.5));
+        Transition tr;
+        int ts = make_transition(p.ell[s], ps, p.eps_B, p.kernel, &tr);
+        if (ts != ADDKER_OK) {
+            cudaFree(a);
+            return ts;
+        }
+        if (w.D == 1) k_coef_sample<1><<<bl, th, 0, st>>>(w.M, p.ell[s], tr, a, b);
+        else if (w.D == 2) k_coef_sample<2><<<bl, th, 0, st>>>(w.M, p.ell[s], tr, a, b);
+        else k_coef_sample<3><<<bl, th, 0, st>>>(w.M, p.ell[s], tr, a, b);
+        // separable DFT along each axis (in place via ping-pong): layout [k0]..[k_{D-1}], last fastest
+        double* dst[2] = {c, d};
+        for (int t = 0; t < w.D; ++t) {
+            int64_t B = 1, A = 1;
+            for (int u = t + 1; u < w.D; ++u) B *= w.M;
+            for (int u = 0; u < t; ++u) A *= w.M;
+            for (int q = 0; q < 2; ++q) {
+                k_coef_dft<<<bl, th, 0, st>>>(src[q], dst[q], (int)A, w.M, (int)B);
+                std::swap(src[q], dst[q]);
+            }
         }
     }
     float* mk[4] = {(float*)w.bK, (float*)w.bD, (float*)w.dconv, (float*)w.chat};
@@ -760,6 +913,19 @@ int setup_window(Plan& p, int s, const float* X, int* keys, int* flag)
         w.twi[t] = tw + (int64_t)w.box[t] * M;
     }
     return ADDKER_OK;
+}
+
+// Per-feature [min, max] of the points into the plan-owned p.range (the separable reading's fit
+// intervals); the points were checked for finiteness and the ball by the cell keys already.
+int feature_range(Plan& p, const float* X)
+{
+    if (p.d > 65535) return ADDKER_EINVAL;
+    CS(dalloc(p, &p.range, 2 * (int64_t)p.d + 1));
+    int* bad = reinterpret_cast<int*>(p.range + 2 * (int64_t)p.d);
+    CK(feature_range_async(X, p.N, p.d, p.range, bad, nullptr));
+    int hbad = 0;
+    CK(cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost));
+    return hbad ? ADDKER_EDOMAIN : ADDKER_OK;
 }
 
 bool valid_stream_ptrs(const void* ptr)
@@ -1075,48 +1241,44 @@ void window_poly_for(int m, double sigma_os, WinPoly* poly)
     fit_window_poly(m, M_PI * (2.0 - 1.0 / sigma_os), poly);
 }
 
-// Fourier multipliers bK, bD, dconv of window w (pointers already set) for length scale ell, computed
-// in the caller's FP64 scratch of at least 4 M^D + M doubles. Enqueued on st and waited for.
-int multipliers_with_scratch(const WinDev& w, double ell, int p_opt, double eps_B, const WinPoly& poly,
+// Fourier multipliers bK, bD, dconv of window w (pointers already set) for length scale ell under the
+// separable reading (axis t is feature t of range: device, per-feature [min, max] of the window's
+// points), computed in the caller's FP64 scratch of at least 2 M^D + 4 M doubles. Enqueued on st and
+// waited for.
+int multipliers_with_scratch(const WinDev& w, double ell, double eps_B, const float* range, const WinPoly& poly,
                              double* scratch, cudaStream_t st)
 {
-    const int ps = p_opt >= 0 ? p_opt : std::max(1, (int)std::floor(w.M * eps_B + 0.5));
-    Transition tr;
-    CS(make_transition(ell, ps, eps_B, ADDKER_KERNEL_GAUSS, &tr));
     int64_t total = 1;
     for (int t = 0; t < w.D; ++t) total *= w.M;
     double* a = scratch;
     double* b = a + total;
-    double* c = b + total;
-    double* d = c + total;
-    double* ph = d + total;
+    double* ph = b + total;
+    double* fit = ph + w.M;
     double phat[kMaxBandwidth];
     window_transform(poly, w.m, w.n, w.M, phat);
     CK(cudaMemcpyAsync(ph, phat, sizeof(double) * w.M, cudaMemcpyHostToDevice, st));
+    const int feat[3] = {0, 1, 2};
+    CK(separable_coefficients(w.D, w.M, ell, eps_B, range, feat, fit, a, b, st));
     const int th = 256, bl = grid_blocks(total, th);
-    if (w.D == 1) k_coef_sample<1><<<bl, th, 0, st>>>(w.M, ell, tr, a, b);
-    else if (w.D == 2) k_coef_sample<2><<<bl, th, 0, st>>>(w.M, ell, tr, a, b);
-    else k_coef_sample<3><<<bl, th, 0, st>>>(w.M, ell, tr, a, b);
-    double* src[2] = {a, b};
-    double* dst[2] = {c, d};
-    for (int t = 0; t < w.D; ++t) {
-        int64_t B = 1, A = 1;
-        for (int u = t + 1; u < w.D; ++u) B *= w.M;
-        for (int u = 0; u < t; ++u) A *= w.M;
-        for (int q = 0; q < 2; ++q) {
-            k_coef_dft<<<bl, th, 0, st>>>(src[q], dst[q], (int)A, w.M, (int)B);
-            std::swap(src[q], dst[q]);
-        }
-    }
     float* bK = const_cast<float*>(w.bK);
     float* bD = const_cast<float*>(w.bD);
     float* dc = const_cast<float*>(w.dconv);
-    if (w.D == 1) k_multipliers<1><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, bK, bD, dc, nullptr);
-    else if (w.D == 2) k_multipliers<2><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, bK, bD, dc, nullptr);
-    else k_multipliers<3><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, bK, bD, dc, nullptr);
+    if (w.D == 1) k_multipliers<1><<<bl, th, 0, st>>>(a, b, w.M, w.n, ph, bK, bD, dc, nullptr);
+    else if (w.D == 2) k_multipliers<2><<<bl, th, 0, st>>>(a, b, w.M, w.n, ph, bK, bD, dc, nullptr);
+    else k_multipliers<3><<<bl, th, 0, st>>>(a, b, w.M, w.n, ph, bK, bD, dc, nullptr);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
     return ADDKER_OK;
+}
+
+// Per-feature [min, max] of X (N x d row-major) into range (2d floats) and *bad = 1 for a value that is
+// not finite; range and *bad are initialised on the device first.
+cudaError_t feature_range_async(const float* X, int64_t N, int d, float* range, int* bad, cudaStream_t st)
+{
+    k_range_init<<<1, 64, 0, st>>>(range, d, bad);
+    const int bx = (int)std::min<int64_t>(64, (N + 255) / 256);
+    k_feature_range<<<dim3(bx, d), 256, 0, st>>>(X, N, d, range, bad);
+    return cudaGetLastError();
 }
 
 // Per-axis twiddles of window w (box and lo set) into tw[t] (forward) and tw[t] + box*M (inverse).
@@ -1158,6 +1320,7 @@ int addker_opts_default(addker_opts* o)
     o->window = ADDKER_WIN_KB;
     o->kernel = ADDKER_KERNEL_GAUSS;
     o->compensated = 0;
+    o->reg = ADDKER_REG_DEFAULT;
     o->stream = nullptr;
     return ADDKER_OK;
 }
@@ -1174,7 +1337,9 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
         return ADDKER_EINVAL;
     if (!(sigma_f > 0.0) || cutoff < 2 || cutoff > 8 || (o.window != ADDKER_WIN_KB && o.window != ADDKER_WIN_ES) ||
         (o.kernel != ADDKER_KERNEL_GAUSS && o.kernel != ADDKER_KERNEL_MATERN12) ||
-        (o.compensated != 0 && o.compensated != 1))
+        (o.compensated != 0 && o.compensated != 1) ||
+        (o.reg != ADDKER_REG_DEFAULT && o.reg != ADDKER_REG_SEPARABLE && o.reg != ADDKER_REG_RADIAL) ||
+        (o.reg == ADDKER_REG_SEPARABLE && o.kernel != ADDKER_KERNEL_GAUSS))
         return ADDKER_EINVAL;
     if (!(o.eps_B > 0.0 && o.eps_B < 0.5) || !(o.sigma_os >= 1.25 && o.sigma_os <= 4.0) || o.p < -1 || o.p > 12)
         return ADDKER_EINVAL;
@@ -1206,6 +1371,8 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
     p.sigma_os = o.sigma_os;
     p.eps_B = o.eps_B;
     p.p_opt = o.p;
+    p.reg = o.reg != ADDKER_REG_DEFAULT ? o.reg
+                                        : (o.kernel == ADDKER_KERNEL_GAUSS ? ADDKER_REG_SEPARABLE : ADDKER_REG_RADIAL);
     p.kernel = o.kernel;
     p.window = o.window;
     p.comp = o.compensated == 1;
@@ -1242,6 +1409,7 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
     }
     for (int s = 0; s < P && status == ADDKER_OK; ++s) status = setup_window(p, s, points, keys, flag);
     if (keys) cudaFree(keys);
+    if (status == ADDKER_OK) status = feature_range(p, points);
     if (status == ADDKER_OK) status = build_items(p, kItemPoints, kItemPoints);
     if (status == ADDKER_OK) status = dalloc(p, &p.wins_dev, P);
     if (status == ADDKER_OK) status = dalloc(p, &p.scale_dev, 3 * P);

@@ -80,6 +80,8 @@ struct Plan {
     int d = 0, P = 0, m = 4;
     double sigma_f = 1.0, sigma_os = 2.0, eps_B = 1.0 / 16.0;
     int p_opt = -1;
+    int reg = ADDKER_REG_SEPARABLE;       // reading of the regularisation (addker_opts.reg, resolved)
+    float* range = nullptr;               // 2d floats: per-feature [min, max] of the points (fit intervals)
     int kernel = ADDKER_KERNEL_GAUSS;     // radial profile family (addker_opts.kernel)
     int window = ADDKER_WIN_KB;           // NFFT window (addker_opts.window)
     bool comp = false;                    // compensated grid accumulation (addker_opts.compensated)
@@ -299,8 +301,9 @@ int gsi_run(Plan& p, const float* v, int cap, int* feats, double* rho, double* t
 
 // Building blocks used without a plan (addker_fastsum_noalloc).
 void window_poly_for(int m, double sigma_os, WinPoly* poly);
-int multipliers_with_scratch(const WinDev& w, double ell, int p_opt, double eps_B, const WinPoly& poly,
+int multipliers_with_scratch(const WinDev& w, double ell, double eps_B, const float* range, const WinPoly& poly,
                              double* scratch, cudaStream_t st);
+cudaError_t feature_range_async(const float* X, int64_t N, int d, float* range, int* bad, cudaStream_t st);
 cudaError_t twiddles_into(const WinDev& w, float2* const tw[3], cudaStream_t st);
 cudaError_t launch_transforms_window(const WinDev& w, const WinDev* w_dev, cudaStream_t st);
 

@@ -1,16 +1,16 @@
 // addker_fastsum_noalloc: the fused product for one window without allocating device memory.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA stream is being captured into a
-// graph (allocation is not a capturable operation), inference servers and real-time loops that
-// forbid device allocation after start-up so memory use stays fixed, and hosts whose allocator owns
-// all device memory (a caching pool that must not be bypassed). For them this entry point takes
-// every working buffer from one fixed array in device memory, declared below at file scope. Every
-// GPU that loads the library keeps that array for the life of the process.
+// Some callers cannot call cudaMalloc: inference servers and real-time loops that forbid device
+// allocation after start-up so that their memory use stays fixed, and hosts whose own allocator owns
+// all device memory (a caching pool that must not be bypassed). For them this entry point takes every
+// working buffer from one fixed array in device memory, declared below at file scope. Every GPU that
+// loads the library keeps that array for the life of the process.
 //
 // The array's limit: one window of d <= 3 features, bandwidth M <= 32 (grid n = 2M <= 64), any N
 // (the points are not sorted, so no buffer grows with N); the layout below must fit kScratchBytes.
 // The variant kernels here spread point by point with atomics into the fixed grid and interpolate
-// point by point; the coefficient precomputation and the transforms are the plan path's own kernels.
+// point by point; the coefficient precomputation (the separable reading, with the fit intervals taken
+// from the points' largest |coordinate| per axis) and the transforms are the plan path's own kernels.
 #include <cstring>
 #include <mutex>
 
@@ -157,9 +157,10 @@ extern "C" int addker_fastsum_noalloc(const float* points, int64_t N, int d, dou
     const size_t o_spec = off; off = align256(off + sizeof(float4) * md);
     const size_t o_mult = off; off = align256(off + sizeof(float) * 3 * md);
     const size_t o_tw = off;   off = align256(off + sizeof(float2) * 2 * (size_t)n * M * D);
-    const size_t o_coef = off; off = align256(off + sizeof(double) * (4 * md + M));
+    const size_t o_coef = off; off = align256(off + sizeof(double) * (2 * md + 4 * M));
     const size_t o_win = off;  off = align256(off + sizeof(WinDev));
     const size_t o_flag = off; off = align256(off + sizeof(int));
+    const size_t o_range = off; off = align256(off + sizeof(float) * 2 * 3 + sizeof(int));
     if (off > kScratchBytes) return ADDKER_ELIMIT;
 
     unsigned char* base = nullptr;
@@ -196,6 +197,8 @@ extern "C" int addker_fastsum_noalloc(const float* points, int64_t N, int d, dou
     }
     WinDev* w_dev = reinterpret_cast<WinDev*>(base + o_win);
     int* flag = reinterpret_cast<int*>(base + o_flag);
+    float* range = reinterpret_cast<float*>(base + o_range);
+    int* bad = reinterpret_cast<int*>(range + 2 * 3);
 
     WinPoly poly;
     window_poly_for(cutoff, sigma_os, &poly);
@@ -204,7 +207,9 @@ extern "C" int addker_fastsum_noalloc(const float* points, int64_t N, int d, dou
     if (cudaMemsetAsync(flag, 0, sizeof(int), st) != cudaSuccess) return ADDKER_ECUDA;
     if (cudaMemcpyAsync(w_dev, &w, sizeof(WinDev), cudaMemcpyHostToDevice, st) != cudaSuccess) return ADDKER_ECUDA;
     if (twiddles_into(w, tw, st) != cudaSuccess) return ADDKER_ECUDA;
-    const int mst = multipliers_with_scratch(w, ell, -1, eps_B, poly, reinterpret_cast<double*>(base + o_coef), st);
+    // the separable reading's fit intervals come from the points' largest |coordinate| per axis
+    if (feature_range_async(points, N, D, range, bad, st) != cudaSuccess) return ADDKER_ECUDA;
+    const int mst = multipliers_with_scratch(w, ell, eps_B, range, poly, reinterpret_cast<double*>(base + o_coef), st);
     if (mst != ADDKER_OK) return mst;
 
     const int th = 128, bl = (int)((N + th - 1) / th);

@@ -24,6 +24,9 @@ ADDKER_WIN_KB = 0
 ADDKER_WIN_ES = 1
 ADDKER_KERNEL_GAUSS = 0
 ADDKER_KERNEL_MATERN12 = 1
+ADDKER_REG_DEFAULT = -1
+ADDKER_REG_SEPARABLE = 0
+ADDKER_REG_RADIAL = 1
 
 
 def ADDKER_ELL(s: int) -> int:
@@ -33,7 +36,7 @@ def ADDKER_ELL(s: int) -> int:
 class addker_opts(ctypes.Structure):
     _fields_ = [("sigma_os", ctypes.c_double), ("eps_B", ctypes.c_double), ("p", ctypes.c_int),
                 ("window", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("compensated", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("compensated", ctypes.c_int), ("reg", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 # name -> (restype, argtypes); every entry point of include/addker.h

@@ -46,7 +46,8 @@ def test_status_codes_match_header():
     text = open(HEADER).read()
     for name in ("ADDKER_OK", "ADDKER_EINVAL", "ADDKER_EDOMAIN", "ADDKER_ENOMEM", "ADDKER_ECUDA",
                  "ADDKER_ETIMEOUT", "ADDKER_ELIMIT", "ADDKER_ELL_SHARED", "ADDKER_SIGMA_F", "ADDKER_WIN_KB",
-                 "ADDKER_WIN_ES", "ADDKER_KERNEL_GAUSS", "ADDKER_KERNEL_MATERN12"):
+                 "ADDKER_WIN_ES", "ADDKER_KERNEL_GAUSS", "ADDKER_KERNEL_MATERN12", "ADDKER_REG_DEFAULT",
+                 "ADDKER_REG_SEPARABLE", "ADDKER_REG_RADIAL"):
         m = re.search(rf"#define {name}\s+\(?(-?\d+)\)?", text)
         assert m and int(m.group(1)) == getattr(native, name), name
 
@@ -59,7 +60,7 @@ def test_strerror_and_defaults(lib):
     assert lib.addker_opts_default(ctypes.byref(o)) == 0
     assert o.sigma_os == 2.0 and o.eps_B == 1 / 16 and o.p == -1 and o.kernel == native.ADDKER_KERNEL_GAUSS
     assert o.window == native.ADDKER_WIN_KB
-    assert o.compensated == 0 and ctypes.sizeof(o) == 40
+    assert o.compensated == 0 and o.reg == native.ADDKER_REG_DEFAULT and ctypes.sizeof(o) == 48
     assert lib.addker_opts_default(None) == native.ADDKER_EINVAL
     assert lib.addker_free(None) == 0
 
@@ -138,6 +139,24 @@ def test_setup_rejects_unknown_window(lib):
     o = native.addker_opts()
     lib.addker_opts_default(ctypes.byref(o))
     o.window = 2
+    plan = ctypes.c_void_p()
+    off = (ctypes.c_int * 2)(0, 3)
+    feat = (ctypes.c_int * 3)(0, 1, 2)
+    ell = (ctypes.c_double * 1)(0.5)
+    bw = (ctypes.c_int * 1)(32)
+    st = lib.addker_setup(ctypes.byref(plan), ctypes.c_void_p(0x1000), 10, 3, off, feat, 1, ell, 1.0, bw, 4,
+                          ctypes.byref(o))
+    assert st == native.ADDKER_EINVAL and not plan.value
+
+
+@pytest.mark.parametrize("kernel,reg", [(0, 2), (0, -2), (1, 0)])
+def test_setup_rejects_bad_regularisation_reading(lib, kernel, reg):
+    """An unknown reading, or the separable reading with Matern(1/2) (whose kernel does not separate),
+    is refused on the host."""
+    from paper_2404_17344_gb300 import native
+    o = native.addker_opts()
+    lib.addker_opts_default(ctypes.byref(o))
+    o.kernel, o.reg = kernel, reg
     plan = ctypes.c_void_p()
     off = (ctypes.c_int * 2)(0, 3)
     feat = (ctypes.c_int * 3)(0, 1, 2)

@@ -24,6 +24,19 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def maxrow(a, b):
+    """Largest single-row error relative to the RMS of the reference: a localised error (a tail item,
+    an edge cell) that the relative L2 norm would average away shows up here. Independent FP32
+    rounding gives a few times the relative L2 error; 10 x TOL is the bar."""
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(np.abs(a - b).max() / (np.linalg.norm(b) / np.sqrt(b.size)))
+
+
+def close(a, b, tol=TOL):
+    return rel(a, b) < tol and maxrow(a, b) < 10 * tol
+
+
 @pytest.fixture(scope="module")
 def torch_cuda():
     import torch
@@ -52,9 +65,9 @@ def test_matvec_all_vs_oracle_nfft(torch_cuda, cfg, N):
     op = make_op(torch, wl)
     Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
     Kr, dKr = oracle_all(wl, v)
-    assert rel(Kv.cpu(), Kr) < TOL
+    assert close(Kv.cpu(), Kr)
     for s in range(wl.P):
-        assert rel(dK[s].cpu(), dKr[s]) < TOL, s
+        assert close(dK[s].cpu(), dKr[s]), s
 
 
 def test_stage_spread_and_adjoint(torch_cuda):
@@ -84,9 +97,9 @@ def test_mixed_window_sizes_and_generic_kernels(torch_cuda):
     op = make_op(torch, wl)
     Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
     Kr, dKr = oracle_all(wl, v)
-    assert rel(Kv.cpu(), Kr) < TOL
+    assert close(Kv.cpu(), Kr)
     for s in range(wl.P):
-        assert rel(dK[s].cpu(), dKr[s]) < TOL, s
+        assert close(dK[s].cpu(), dKr[s]), s
 
 
 @pytest.mark.parametrize("M", [12, 20, 64])
@@ -116,14 +129,33 @@ def test_other_cutoffs(torch_cuda, m):
 
 
 @pytest.mark.parametrize("p", [0, 1, 4])
-def test_regularisation_degrees(torch_cuda, p):
+def test_radial_regularisation_degrees(torch_cuda, p):
     torch = torch_cuda
     wl = workloads.make("c0", N=3000)
     v = wl.vector()
-    op = make_op(torch, wl, p=p)
+    op = make_op(torch, wl, p=p, reg="radial")
     Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
-    Kr, dKr = oracle_all(wl, v, p=p)
+    Kr, dKr = oracle_all(wl, v, p=p, reg="radial")
     assert rel(Kv.cpu(), Kr) < TOL and rel(dK.cpu(), dKr) < TOL
+
+
+@pytest.mark.parametrize("cfg,N", [("c1", 20000), ("c3", 20000)])
+def test_separable_reading_against_the_direct_sums(torch_cuda, cfg, N):
+    """The default reading end to end: the GPU products against the oracle's CPU NFFT with the same
+    separable coefficients (1e-5), and against the FP64 direct sums on 1000 rows within the oracle's
+    own Fourier error plus 1e-5 (windows of 1, 2 and 3 features, bandwidths 16 and 32)."""
+    torch = torch_cuda
+    wl = workloads.make(cfg, N=N)
+    v = wl.vector()
+    Kv, dK = make_op(torch, wl).matvec_all(torch.from_numpy(v).cuda())
+    Kv, dK = Kv.cpu().numpy(), dK.cpu().numpy()
+    Kr, dKr = oracle_all(wl, v)
+    assert rel(Kv, Kr) < TOL and all(rel(dK[s], dKr[s]) < TOL for s in range(wl.P))
+    rows = np.random.default_rng(3).choice(wl.N, 1000, replace=False)
+    Kd, dKd = fastsum.direct(wl.points, wl.windows, wl.ell, wl.sigma_f, v.astype(np.float64), rows=rows)
+    assert rel(Kv[rows], Kd) < rel(Kr[rows], Kd) + TOL
+    for s in range(wl.P):
+        assert rel(dK[s, rows], dKd[s]) < rel(dKr[s, rows], dKd[s]) + TOL, s
 
 
 def test_dmatvec_selectors_and_multi_rhs(torch_cuda):
@@ -159,6 +191,32 @@ def test_host_buffers_entry(torch_cuda):
     dKh = torch.empty(wl.N * wl.P).pin_memory()
     op.matvec_all_host(vh, Kh, dKh)
     assert rel(Kh, Kd.cpu()) < TOL and rel(dKh.reshape(wl.P, wl.N), dKd.cpu()) < TOL
+    Kr, dKr = oracle_all(wl, v)
+    assert close(Kh, Kr)
+    for s in range(wl.P):
+        assert close(dKh.reshape(wl.P, wl.N)[s], dKr[s]), s
+
+
+@pytest.mark.slow
+def test_host_buffers_entry_full_size_against_the_oracle(torch_cuda):
+    """The host-buffer entry at one right-hand side and three windows (its own path: per-window gathers
+    with each window's copy overlapped) at the benchmark's size, N = 1e6, against the oracle's CPU NFFT
+    on 4096 sampled rows."""
+    torch = torch_cuda
+    wl = workloads.make("c1", N=1_000_000)
+    v = wl.vector()
+    op = make_op(torch, wl)
+    vh = torch.from_numpy(v).pin_memory()
+    Kh = torch.empty(wl.N).pin_memory()
+    dKh = torch.empty(wl.N * wl.P).pin_memory()
+    op.matvec_all_host(vh, Kh, dKh)
+    op.matvec_all_host(vh, Kh, dKh)                   # the second call replays a captured graph
+    Kh, dKh = Kh.numpy(), dKh.numpy().reshape(wl.P, wl.N)
+    rows = np.random.default_rng(11).choice(wl.N, 4096, replace=False)
+    Kn, dKn = oracle_all(wl, v, rows=rows)
+    assert close(Kh[rows], Kn)
+    for s in range(wl.P):
+        assert close(dKh[s, rows], dKn[s]), s
 
 
 def test_set_params(torch_cuda):
