@@ -179,12 +179,15 @@ def default_reg(kernel: str) -> str:
 
 
 def coefficients_for(xs: np.ndarray, ell: float, M: int, p=None, eps_B: float = 1.0 / 16.0,
-                     kernel: str = "gauss", reg: str | None = None):
-    """(c_hat, c_hat^der) of one window whose source points (N x d_s, the window's coordinates) are xs.
+                     kernel: str = "gauss", reg: str | None = None, split: bool = True):
+    """(c_hat, c_hat^der, q) of one window whose source points (N x d_s, the window's coordinates) are xs.
 
     reg 'separable' (default for the Gaussian): kernels.coefficients_separable on the fit intervals
     a_t of every axis, computed from the largest |coordinate| of xs; reg 'radial': the radial
-    regularisation of degree p (kernels.default_p when None)."""
+    regularisation of degree p (kernels.default_p when None). Under the separable reading the window's
+    quadratic part is split off when kernels.split_quadratic says so (and `split` allows it): then
+    c_hat^der is the remainder's, and q = 1/(2 ell^2) is the weight of kernels.quadratic_part that every
+    derivative product adds; q = 0 otherwise."""
     reg = default_reg(kernel) if reg is None else reg
     d = xs.shape[1]
     if reg == "separable":
@@ -192,12 +195,16 @@ def coefficients_for(xs: np.ndarray, ell: float, M: int, p=None, eps_B: float = 
             raise ValueError("the separable reading covers the Gaussian family only")
         maxabs = np.abs(xs).max(axis=0) if xs.shape[0] else np.zeros(d)
         iv = [kernels.fit_interval(float(a), M, eps_B) for a in maxabs]
-        return (kernels.coefficients_separable(ell, M, iv, "gauss"),
-                kernels.coefficients_separable(ell, M, iv, "der"))
+        cg = kernels.coefficients_separable(ell, M, iv, "gauss")
+        cd = kernels.coefficients_separable(ell, M, iv, "der")
+        cp = kernels.coefficients_separable(ell, M, iv, "quad")
+        if split and kernels.split_quadratic(cd, cp):
+            return cg, cd - cp, 1.0 / (2.0 * ell * ell)
+        return cg, cd, 0.0
     if reg != "radial":
         raise ValueError(reg)
     ps = kernels.default_p(M, eps_B) if p is None else int(p)
-    return window_coefficients(ell, d, M, ps, eps_B, kernel)
+    return window_coefficients(ell, d, M, ps, eps_B, kernel) + (0.0,)
 
 
 def direct_matern(points, windows, ell, sigma_f: float, v, rows=None, block: int = 256):
@@ -223,13 +230,14 @@ def direct_matern(points, windows, ell, sigma_f: float, v, rows=None, block: int
 
 def matvec_all(points, windows, ell, sigma_f: float, v, bandwidth, cutoff: int, p=None,
                eps_B: float = 1.0 / 16.0, sigma: float = 2.0, level: str = "nfft", rows=None,
-               kernel: str = "gauss", win: str = "kb", reg: str | None = None, coefs=None):
+               kernel: str = "gauss", win: str = "kb", reg: str | None = None, coefs=None, split: bool = True):
     """Fused product: returns (K v, dK/d ell [P, .]) at level 'nfft' (CPU NFFT fast sum)
     or 'ndft' (exact trigonometric sum). v is one right-hand side of length N. With `rows`, the
     outputs are evaluated only at those points (all N points are still sources). `win` selects the
     NFFT window ('kb' Kaiser-Bessel, 'es' exponential of semicircle); `reg` the reading of the
-    regularisation (coefficients_for). `coefs` may hold the P pairs (c_hat, c_hat^der) from an earlier
-    call (they depend only on the points' extents and the hyperparameters)."""
+    regularisation (coefficients_for), `split` whether a window's quadratic part may be split off.
+    `coefs` may hold the P triples (c_hat, c_hat^der, q) from an earlier call (they depend only on the
+    points' extents and the hyperparameters)."""
     X = np.asarray(points, dtype=np.float32).astype(np.float64)
     v = np.asarray(v, dtype=np.float64)
     P = len(windows)
@@ -244,9 +252,9 @@ def matvec_all(points, windows, ell, sigma_f: float, v, bandwidth, cutoff: int, 
         M = int(bandwidth[s])
         xs = np.ascontiguousarray(X[:, list(w)])
         if coefs is not None:
-            cg, cd = coefs[s]
+            cg, cd, q = coefs[s]
         else:
-            cg, cd = coefficients_for(xs, float(ell[s]), M, p, eps_B, kernel, reg)
+            cg, cd, q = coefficients_for(xs, float(ell[s]), M, p, eps_B, kernel, reg, split)
         xt = None if rows is None else np.ascontiguousarray(T[:, list(w)])
         if level == "nfft":
             outK, outD = nfft_fastsum(xs, v, [cg, cd], int(round(sigma * M)), cutoff, sigma, targets=xt, win=win)
@@ -256,6 +264,8 @@ def matvec_all(points, windows, ell, sigma_f: float, v, bandwidth, cutoff: int, 
             outK, outD = ndft_fastsum(xs, v, [cg, cd])
         else:
             raise ValueError(level)
+        if q:
+            outD = outD + q * kernels.quadratic_part(xs, v, None if rows is None else xt)
         Kv += sigma_f ** 2 * outK
         dK[s] = sigma_f ** 2 * (KINDS[kernel][2] / ell[s]) * outD
     return Kv, dK

@@ -82,7 +82,7 @@ def nfft_grad(points, windows, ell, sigma_f, v, w, bandwidth, cutoff, p=None, ep
         M = int(bandwidth[s])
         n = int(round(sigma * M))
         xs = np.ascontiguousarray(X[:, list(win)])
-        cg, _ = fastsum.coefficients_for(xs, float(ell[s]), M, p, eps_B, "gauss", reg)
+        cg, _, _ = fastsum.coefficients_for(xs, float(ell[s]), M, p, eps_B, "gauss", reg)
         _, gv = gather_grad(xs, _grid(xs, v, cg, n, cutoff, sigma), n, cutoff, sigma)
         _, gw = gather_grad(xs, _grid(xs, w, cg, n, cutoff, sigma), n, cutoff, sigma)
         gx[:, list(win)] += sigma_f ** 2 * (w[:, None] * gv + v[:, None] * gw)

@@ -26,7 +26,7 @@ from . import fastsum
 def window_spectrum(points, window, ell: float, v, M: int, p=None, eps_B: float = 1.0 / 16.0, reg=None):
     """c_hat_k S(k, W) for k in I_M^d (array indexed k + M/2), S by the exact trigonometric sum."""
     x = np.asarray(points, dtype=np.float32).astype(np.float64)[:, list(window)]
-    chat, _ = fastsum.coefficients_for(x, float(ell), M, p, eps_B, "gauss", reg)
+    chat, _, _ = fastsum.coefficients_for(x, float(ell), M, p, eps_B, "gauss", reg)
     S = fastsum.adjoint_exact(x, np.asarray(v, dtype=np.float64), M)
     return chat * S
 

@@ -205,9 +205,8 @@ def coefficients_separable(ell: float, M: int, intervals, kind: str = "gauss") -
     """c_hat_k for k in I_M^d (d = len(intervals)), shape (M,)*d indexed k + M/2, of the separable
     reading: the tensor product of the 1-D factors (kind 'gauss') or the d-term sum with one factor g
     (kind 'der'), Sec. 3.4."""
-    if kind not in ("gauss", "der"):
+    if kind not in ("gauss", "der", "quad"):
         raise ValueError("the separable reading covers the Gaussian family only")
-    f = [factor_coefficients(ell, a, M, "gauss") for a in intervals]
 
     def outer(fs):
         out = fs[0]
@@ -215,7 +214,45 @@ def coefficients_separable(ell: float, M: int, intervals, kind: str = "gauss") -
             out = np.multiply.outer(out, q)
         return out
 
+    d = len(intervals)
+    if kind == "quad":
+        # P(r) = ||r||^2 / (2 ell^2) = sum_t p(r_t): one factor p, the others the constant 1 (c_0 = 1)
+        one = np.zeros(M)
+        one[M // 2] = 1.0
+        pf = [cosine_extension(extension_nodes(a, M) ** 2 / (2.0 * ell * ell), a, M) for a in intervals]
+        return sum(outer([pf[t] if u == t else one for u in range(d)]) for t in range(d))
+    f = [factor_coefficients(ell, a, M, "gauss") for a in intervals]
     if kind == "gauss":
         return outer(f)
     g = [factor_coefficients(ell, a, M, "der") for a in intervals]
-    return sum(outer([g[t] if u == t else f[u] for u in range(len(f))]) for t in range(len(f)))
+    return sum(outer([g[t] if u == t else f[u] for u in range(d)]) for t in range(d))
+
+
+# ------------------------------------------------------------ the quadratic part, split off ----
+# For a wide kernel (ell large against the data) kappa_der(r) = q e^{-q}, q = ||r||^2/(2 ell^2), is close
+# to its quadratic part P(r) = q. A trigonometric polynomial represents the quadratic on the torus with a
+# large constant term that cancels against the low frequencies inside the data ball (about 24 times the
+# product at ell = 1 on the benchmark's windows), which multiplies every FP32 rounding of the transforms
+# by that factor. P is a rank-5 kernel, so P v needs no transform at all:
+#     sum_j ||x_i - x_j||^2 v_j = ||x_i||^2 m0 - 2 x_i . m1 + m2,
+#     m0 = sum_j v_j,  m1 = sum_j x_j v_j,  m2 = sum_j ||x_j||^2 v_j,
+# and the fast summation then carries only the remainder R = kappa_der - P, whose coefficients are
+# c_hat^der - c_hat^P (the same least-squares factors, kind 'quad'). For a narrow kernel R is no smaller
+# than kappa_der and splitting would enlarge the transforms' terms instead, so a window is split only
+# when that shrinks the constant coefficient: |c_0^der - c_0^P| < 0.9 |c_0^der|.
+
+def split_quadratic(cd: np.ndarray, cp: np.ndarray) -> bool:
+    """The rule above, from the coefficient arrays of kappa_der and of P (constant term at the centre)."""
+    c = tuple(n // 2 for n in cd.shape)
+    return abs(cd[c] - cp[c]) < 0.9 * abs(cd[c])
+
+
+def quadratic_part(xs: np.ndarray, v: np.ndarray, targets: np.ndarray | None = None) -> np.ndarray:
+    """sum_j ||x_i - x_j||^2 v_j for every target x_i (the sources xs by default), through the moments."""
+    xs = np.asarray(xs, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    t = xs if targets is None else np.asarray(targets, dtype=np.float64)
+    m0 = v.sum()
+    m1 = xs.T @ v
+    m2 = (xs * xs).sum(axis=1) @ v
+    return (t * t).sum(axis=1) * m0 - 2.0 * (t @ m1) + m2

@@ -145,8 +145,8 @@ def test_sigma_f_and_derivative_scalings():
     X = wl.points.astype(np.float64)
     for s, w in enumerate(wl.windows):
         xs = np.ascontiguousarray(X[:, list(w)])
-        _, cd = fastsum.coefficients_for(xs, wl.ell[s], 16)
-        raw = fastsum.nfft_fastsum(xs, v, [cd], 32, 4)[0]
+        _, cd, q = fastsum.coefficients_for(xs, wl.ell[s], 16)
+        raw = fastsum.nfft_fastsum(xs, v, [cd], 32, 4)[0] + q * kernels.quadratic_part(xs, v)
         np.testing.assert_allclose(D1[s], 2.0 / wl.ell[s] * raw, rtol=1e-13)
 
 

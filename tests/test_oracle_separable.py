@@ -141,12 +141,12 @@ def test_separable_fast_sum_within_hoelder_bound_of_direct():
     X = wl.points[idx]
     v = rng.standard_normal(1500)
     Kd, Dd = fastsum.direct(X, wl.windows, wl.ell, 1.0, v)
-    Kt, Dt = fastsum.matvec_all(X, wl.windows, wl.ell, 1.0, v, 32, 4, level="ndft")
+    Kt, Dt = fastsum.matvec_all(X, wl.windows, wl.ell, 1.0, v, 32, 4, level="ndft", split=False)
     assert rel(Kt, Kd) < 1e-6
     for s, w in enumerate(wl.windows):
         assert rel(Dt[s], Dd[s]) < 1e-5
         xs = X[:, list(w)].astype(np.float64)
-        cg, cd = fastsum.coefficients_for(xs, wl.ell[s], 32)
+        cg, cd, _ = fastsum.coefficients_for(xs, wl.ell[s], 32, split=False)
         r = (xs[:300, None, :] - xs[None, :, :]).reshape(-1, 3)
         sup = np.abs(kernels.trig_poly_eval(cd, r) - kernels.kappa(np.linalg.norm(r, axis=1), wl.ell[s], "der")).max()
         one = fastsum.ndft_fastsum(xs, v, [cd])[0][:300]
@@ -164,7 +164,7 @@ def test_separable_beats_radial_against_direct():
     X = wl.points[idx]
     v = rng.standard_normal(1200)
     _, Dd = fastsum.direct(X, wl.windows, wl.ell, 1.0, v)
-    _, Ds = fastsum.matvec_all(X, wl.windows, wl.ell, 1.0, v, 32, 4, level="ndft")
+    _, Ds = fastsum.matvec_all(X, wl.windows, wl.ell, 1.0, v, 32, 4, level="ndft", split=False)
     _, Dr = fastsum.matvec_all(X, wl.windows, wl.ell, 1.0, v, 32, 4, level="ndft", reg="radial")
     for s in range(wl.P):
         assert rel(Ds[s], Dd[s]) * 10 < rel(Dr[s], Dd[s])
@@ -174,5 +174,69 @@ def test_matern_rejects_the_separable_reading():
     xs = np.zeros((4, 2))
     with pytest.raises(ValueError):
         fastsum.coefficients_for(xs, 0.3, 16, kernel="matern", reg="separable")
-    cg, _ = fastsum.coefficients_for(xs, 0.3, 16, kernel="matern")
+    cg, _, q = fastsum.coefficients_for(xs, 0.3, 16, kernel="matern")
+    assert q == 0.0
     np.testing.assert_array_equal(cg, kernels.coefficients(0.3, 2, 16, kernels.default_p(16, 1 / 16), 1 / 16, "matern"))
+
+
+# --------------------------------------------------------------------- quadratic split ----
+
+def test_quadratic_part_is_the_brute_force_sum():
+    """sum_j ||x_i - x_j||^2 v_j through the moments equals the double loop (targets = sources and a
+    separate target set)."""
+    rng = np.random.default_rng(12)
+    x = rng.uniform(-0.2, 0.2, (40, 3))
+    t = rng.uniform(-0.2, 0.2, (7, 3))
+    v = rng.standard_normal(40)
+    for tg in (None, t):
+        tt = x if tg is None else tg
+        want = np.array([sum(float(np.sum((tt[i] - x[j]) ** 2)) * v[j] for j in range(40)) for i in range(len(tt))])
+        np.testing.assert_allclose(kernels.quadratic_part(x, v, tg), want, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_quadratic_coefficients_represent_the_quadratic(d):
+    """c_hat^P (kind 'quad') evaluated as a trigonometric polynomial is ||r||^2/(2 ell^2) on the box of the
+    fit intervals, within the 1-D fit's error."""
+    M, ell = 32, 0.7
+    iv = [0.3, 0.38, 0.42][:d]
+    c = kernels.coefficients_separable(ell, M, iv, "quad")
+    rng = np.random.default_rng(13)
+    r = rng.uniform(-1, 1, (3000, d)) * np.asarray(iv)
+    want = (r * r).sum(axis=1) / (2 * ell * ell)
+    e1 = 0.0                                     # the 1-D fits' sup errors on their intervals, summed
+    for a in iv:
+        xx = np.linspace(0, a, 3001)
+        ca = kernels.cosine_extension(kernels.extension_nodes(a, M) ** 2 / (2 * ell * ell), a, M)
+        e1 += np.abs(cos_eval(ca, xx) - xx ** 2 / (2 * ell * ell)).max()
+    assert np.abs(kernels.trig_poly_eval(c, r) - want).max() <= e1 * 1.01 + 1e-15
+    assert e1 < 1e-5 * want.max()
+
+
+def test_split_rule_on_the_benchmark_windows():
+    """The quadratic part is split off for the wide kernels (ell = 0.5, 1.0) of the benchmark's windows and
+    kept for the narrow one (ell = 0.3), where the remainder would carry a larger constant term."""
+    wl = workloads.make("c1", N=200_000)
+    got = [fastsum.coefficients_for(np.ascontiguousarray(wl.points[:, list(w)].astype(np.float64)), wl.ell[s], 32)[2]
+           for s, w in enumerate(wl.windows)]
+    assert got[0] == 0.0 and got[1] == pytest.approx(2.0) and got[2] == pytest.approx(0.5)
+
+
+def test_split_product_equals_the_unsplit_one_within_the_fit_error():
+    """Remainder-by-transform plus quadratic-by-moments is the same approximation of the derivative product
+    up to the fit error of the quadratic's own extension (which the split no longer needs), and both meet
+    the direct sums."""
+    wl = workloads.make("c1", N=1_000_000)
+    rng = np.random.default_rng(14)
+    idx = rng.choice(wl.N, 1500, replace=False)
+    X = wl.points[idx]
+    v = rng.standard_normal(1500)
+    _, Dd = fastsum.direct(X, wl.windows, wl.ell, 1.0, v)
+    _, Ds = fastsum.matvec_all(X, wl.windows, wl.ell, 1.0, v, 32, 4, level="ndft")
+    _, Du = fastsum.matvec_all(X, wl.windows, wl.ell, 1.0, v, 32, 4, level="ndft", split=False)
+    for s in range(wl.P):
+        assert rel(Ds[s], Du[s]) < 1e-5
+        assert rel(Ds[s], Dd[s]) < 1e-5
+    _, Dn = fastsum.matvec_all(X, wl.windows, wl.ell, 1.0, v, 32, 4)          # CPU NFFT, split
+    for s in range(wl.P):
+        assert rel(Dn[s], Ds[s]) < 1e-6
