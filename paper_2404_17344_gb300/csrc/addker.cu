@@ -204,10 +204,10 @@ __global__ void k_coef_sample(int M, double ell, Transition tr, double* __restri
 // fitted on J = 4M equispaced nodes a_t i/(J-1) by cos(2 pi k x), k < K = M/2. The floor keeps the
 // basis well conditioned (condition number below ~1e5); the fit is already within 1e-8 there.
 
-// One block per axis t: Householder QR of the J x K cosine matrix with the two right-hand sides f, g
-// appended (J x (K+2), column-major in dynamic shared memory), then back substitution.
+// One block per axis t: Householder QR of the J x K cosine matrix with the three right-hand sides f, g and
+// p(x) = x^2/(2 ell^2) appended (J x (K+3), column-major in dynamic shared memory), then back substitution.
 // range: per-feature [min, max] of the points (2 floats per feature); feat[t]: the axis's feature.
-// out[(2t + q) K + k] = b_k of f (q = 0) or g (q = 1).
+// out[(3t + q) K + k] = b_k of f (q = 0), g (q = 1) or p (q = 2).
 __global__ void k_fit_extension(int M, double ell, double eps_B, const float* __restrict__ range, int f0, int f1,
                                 int f2, double* __restrict__ out)
 {
@@ -216,7 +216,7 @@ __global__ void k_fit_extension(int M, double ell, double eps_B, const float* __
     __shared__ double s_beta, s_alpha;
     const int t = blockIdx.x;
     const int f = t == 0 ? f0 : (t == 1 ? f1 : f2);
-    const int J = 4 * M, K = M / 2, C = K + 2;
+    const int J = 4 * M, K = M / 2, C = K + 3;
     const double maxabs = fmax(-(double)range[2 * f], (double)range[2 * f + 1]);
     const double a = fmin(0.5 - eps_B, fmax(fmax(0.25, 0.5 - 4.0 / M), 2.0 * maxabs));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -226,6 +226,7 @@ __global__ void k_fit_extension(int M, double ell, double eps_B, const float* __
         const double q = x * x / (2.0 * ell * ell), e = exp(-q);
         A[K * J + i] = e;
         A[(K + 1) * J + i] = q * e;
+        A[(K + 2) * J + i] = q;
     }
     __syncthreads();
     for (int c = 0; c < K; ++c) {
@@ -257,58 +258,69 @@ __global__ void k_fit_extension(int M, double ell, double eps_B, const float* __
         if (tid == 0) A[c * J + c] = s_alpha;              // R's diagonal
         __syncthreads();
     }
-    if (tid < 2) {                                         // R b = (Q^T rhs)[0..K), R[k][j] = A[j J + k]
+    if (tid < 3) {                                         // R b = (Q^T rhs)[0..K), R[k][j] = A[j J + k]
         double x[kMaxBandwidth / 2];
         for (int k = K - 1; k >= 0; --k) {
             double acc = A[(K + tid) * J + k];
             for (int j = k + 1; j < K; ++j) acc -= A[j * J + k] * x[j];
             x[k] = acc / A[k * J + k];
         }
-        for (int k = 0; k < K; ++k) out[(2 * t + tid) * K + k] = x[k];
+        for (int k = 0; k < K; ++k) out[(3 * t + tid) * K + k] = x[k];
     }
 }
 
-// c_hat and c_hat^der on I_M^D (layout [k_0]..[k_{D-1}], last fastest) from the fitted factors:
-// c_{k}(.) = b_0 at k = 0, b_|k| / 2 for 0 < |k| < M/2, 0 at k = -M/2.
+// c_hat, c_hat^der and the quadratic's c_hat^P on I_M^D (layout [k_0]..[k_{D-1}], last fastest) from the
+// fitted factors: c_{k}(.) = b_0 at k = 0, b_|k| / 2 for 0 < |k| < M/2, 0 at k = -M/2;
+// c^P_k = sum_t c_{k_t}(p) prod_{u != t} [k_u = 0] (P(r) = sum_t p(r_t)).
 template <int D>
 __global__ void k_coef_tensor(int M, const double* __restrict__ fit, double* __restrict__ outK,
-                              double* __restrict__ outD)
+                              double* __restrict__ outD, double* __restrict__ outP)
 {
     int64_t total = 1;
     for (int t = 0; t < D; ++t) total *= M;
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= total) return;
     const int K = M / 2;
-    double fv[3], gv[3];
+    double fv[3], gv[3], pv[3];
+    int zero[3];
     int64_t rem = idx;
     for (int t = D - 1; t >= 0; --t) {
         const int k = (int)(rem % M) - K;
         rem /= M;
         const int ak = k < 0 ? -k : k;
-        const double* bf = fit + (2 * t) * K;
-        const double* bg = fit + (2 * t + 1) * K;
-        if (ak >= K) { fv[t] = 0.0; gv[t] = 0.0; }
-        else if (ak == 0) { fv[t] = bf[0]; gv[t] = bg[0]; }
-        else { fv[t] = 0.5 * bf[ak]; gv[t] = 0.5 * bg[ak]; }
+        const double* bf = fit + (3 * t) * K;
+        const double* bg = fit + (3 * t + 1) * K;
+        const double* bp = fit + (3 * t + 2) * K;
+        zero[t] = k == 0;
+        if (ak >= K) { fv[t] = 0.0; gv[t] = 0.0; pv[t] = 0.0; }
+        else if (ak == 0) { fv[t] = bf[0]; gv[t] = bg[0]; pv[t] = bp[0]; }
+        else { fv[t] = 0.5 * bf[ak]; gv[t] = 0.5 * bg[ak]; pv[t] = 0.5 * bp[ak]; }
     }
-    double cK = 1.0, cD = 0.0;
+    double cK = 1.0, cD = 0.0, cP = 0.0;
     for (int t = 0; t < D; ++t) {
         double term = gv[t];
-        for (int u = 0; u < D; ++u) if (u != t) term *= fv[u];
+        bool others_zero = true;
+        for (int u = 0; u < D; ++u)
+            if (u != t) {
+                term *= fv[u];
+                others_zero = others_zero && zero[u];
+            }
         cD += term;
+        if (others_zero) cP += pv[t];
         cK *= fv[t];
     }
     outK[idx] = cK;
     outD[idx] = cD;
+    outP[idx] = cP;
 }
 
-// Enqueue the separable coefficients of one window (D axes, features feat[0..D)) into cK, cD (M^D
-// doubles each), using fit (2 D K doubles) for the 1-D factors.
+// Enqueue the separable coefficients of one window (D axes, features feat[0..D)) into cK, cD, cP (M^D
+// doubles each), using fit (3 D K doubles) for the 1-D factors.
 cudaError_t separable_coefficients(int D, int M, double ell, double eps_B, const float* range, const int* feat,
-                                   double* fit, double* cK, double* cD, cudaStream_t st)
+                                   double* fit, double* cK, double* cD, double* cP, cudaStream_t st)
 {
     const int J = 4 * M, K = M / 2;
-    const size_t shm = sizeof(double) * (size_t)J * (K + 2);
+    const size_t shm = sizeof(double) * (size_t)J * (K + 3);
     cudaError_t e = cudaFuncSetAttribute(k_fit_extension, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
     k_fit_extension<<<D, 128, shm, st>>>(M, ell, eps_B, range, feat[0], D > 1 ? feat[1] : 0, D > 2 ? feat[2] : 0,
@@ -316,10 +328,32 @@ cudaError_t separable_coefficients(int D, int M, double ell, double eps_B, const
     int64_t total = 1;
     for (int t = 0; t < D; ++t) total *= M;
     const int th = 256, bl = (int)((total + th - 1) / th);
-    if (D == 1) k_coef_tensor<1><<<bl, th, 0, st>>>(M, fit, cK, cD);
-    else if (D == 2) k_coef_tensor<2><<<bl, th, 0, st>>>(M, fit, cK, cD);
-    else k_coef_tensor<3><<<bl, th, 0, st>>>(M, fit, cK, cD);
+    if (D == 1) k_coef_tensor<1><<<bl, th, 0, st>>>(M, fit, cK, cD, cP);
+    else if (D == 2) k_coef_tensor<2><<<bl, th, 0, st>>>(M, fit, cK, cD, cP);
+    else k_coef_tensor<3><<<bl, th, 0, st>>>(M, fit, cK, cD, cP);
     return cudaGetLastError();
+}
+
+// The quadratic split. For a kernel wide against the data the derivative kernel q e^{-q},
+// q = ||r||^2/(2 ell^2), is nearly its quadratic part P = q; as a trigonometric polynomial P needs a
+// constant term many times the product (about 24 times at ell = 1 on the nine-feature benchmark) that
+// cancels against the low frequencies, and every FP32 rounding in the transforms is multiplied by that
+// factor. P is a rank-5 kernel (sum_j ||x_i - x_j||^2 v_j = ||x_i||^2 m0 - 2 x_i.m1 + m2 with the
+// moments m0 = sum v, m1 = sum x v, m2 = sum ||x||^2 v), so a split window sends only the remainder
+// c_hat^der - c_hat^P through the transforms and adds P v from moments the spread accumulates. Rule:
+// split when that shrinks the constant coefficient, |c_0^der - c_0^P| < 0.9 |c_0^der| (for a narrow
+// kernel the remainder would be the larger one). Reads the two constant terms.
+int decide_split(int D, int M, const double* cD, const double* cP, cudaStream_t st, bool* split)
+{
+    int64_t c = 0;
+    for (int t = 0; t < D; ++t) c = c * M + M / 2;
+    double h[2];
+    if (cudaMemcpyAsync(&h[0], cD + c, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&h[1], cP + c, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return ADDKER_ECUDA;
+    *split = std::fabs(h[0] - h[1]) < 0.9 * std::fabs(h[0]);
+    return ADDKER_OK;
 }
 
 // out[a][k][b] = (1/M) sum_j in[a][j][b] cos(2 pi (j - M/2)(k - M/2) / M); the sine part of the DFT
@@ -343,10 +377,11 @@ __global__ void k_coef_dft(const double* __restrict__ in, double* __restrict__ o
 
 // bK = c_hat / (n^D prod_t phi_hat(k_t))^2, bD likewise, dconv = 1 / (n^D prod_t phi_hat(k_t)),
 // with phat[k + M/2] the Fourier transform of the window the kernels spread with.
+// With cP (not NULL) the derivative multiplier is that of the remainder c_hat^der - c_hat^P (quadratic split).
 template <int D>
 __global__ void k_multipliers(const double* __restrict__ cK, const double* __restrict__ cD, int M, int n,
                               const double* __restrict__ phat, float* __restrict__ bK, float* __restrict__ bD,
-                              float* __restrict__ dconv, float* __restrict__ chat)
+                              float* __restrict__ dconv, float* __restrict__ chat, const double* __restrict__ cP)
 {
     int64_t total = 1;
     for (int t = 0; t < D; ++t) total *= M;
@@ -361,7 +396,7 @@ __global__ void k_multipliers(const double* __restrict__ cK, const double* __res
     }
     double den = nd * ph;
     bK[idx] = (float)(cK[idx] / (den * den));
-    bD[idx] = (float)(cD[idx] / (den * den));
+    bD[idx] = (float)((cP ? cD[idx] - cP[idx] : cD[idx]) / (den * den));
     dconv[idx] = (float)(1.0 / den);
     if (chat) chat[idx] = (float)cK[idx];
 }
@@ -411,14 +446,26 @@ __global__ void k_window_sum(const float* __restrict__ ks, int P, int64_t N, flo
 
 struct ThetaScale {
     double s[2 * kMaxWindows + 1];       // [0,P): sigma_f^2 2/ell_s ; P: 2 sigma_f
+    double q[kMaxWindows];               // the quadratic split's weight 1/(2 ell_s^2), or 0
 };
 
-// grad_theta[s] = sigma_f^2 (2/ell_s) dots[P + s]  (s < P);  grad_theta[P] = 2 sigma_f sum_s dots[s]
-__global__ void k_theta_grad(const double* __restrict__ dots, int P, ThetaScale sc, double* __restrict__ out)
+// grad_theta[s] = sigma_f^2 (2/ell_s) (dots[P + s] + v^T P_s w)  (s < P);  grad_theta[P] = 2 sigma_f sum_s dots[s].
+// For a split window the remainder's part is in dots and the quadratic part comes from the moments of
+// v (mv) and of w (mw): v^T P w = q (m0(v) m2(w) - 2 m1(v).m1(w) + m2(v) m0(w)).
+__global__ void k_theta_grad(const double* __restrict__ dots, int P, ThetaScale sc, const double* __restrict__ mv,
+                             const double* __restrict__ mw, double* __restrict__ out)
 {
     grid_dep_wait();
     const int s = threadIdx.x;
-    if (s < P) out[s] = sc.s[s] * dots[P + s];
+    if (s < P) {
+        double d = dots[P + s];
+        if (sc.q[s] != 0.0) {
+            const double* a = mv + 8 * s;
+            const double* b = mw + 8 * s;
+            d += sc.q[s] * (a[0] * b[4] - 2.0 * (a[1] * b[1] + a[2] * b[2] + a[3] * b[3]) + a[4] * b[0]);
+        }
+        out[s] = sc.s[s] * d;
+    }
     if (s == 0) {
         double acc = 0.0;
         for (int q = 0; q < P; ++q) acc += dots[q];
@@ -741,13 +788,15 @@ int compute_multipliers(Plan& p, int s)
     WinDev& w = p.win[s];
     int64_t total = 1;
     for (int t = 0; t < w.D; ++t) total *= w.M;
-    double *a = nullptr, *b = nullptr, *c = nullptr, *d = nullptr, *ph = nullptr, *fit = nullptr;
-    CK(cudaMalloc(&a, sizeof(double) * (total * 4 + 4 * w.M)));
+    double *a = nullptr, *b = nullptr, *c = nullptr, *d = nullptr, *ph = nullptr, *fit = nullptr, *cp = nullptr;
+    CK(cudaMalloc(&a, sizeof(double) * (total * 5 + 6 * w.M)));
     b = a + total;
     c = b + total;
     d = c + total;
-    ph = d + total;
-    fit = ph + w.M;                                   // 2 D (M/2) <= 3 M doubles
+    cp = d + total;
+    ph = cp + total;
+    fit = ph + w.M;                                   // 3 D (M/2) <= 4.5 M doubles
+    bool split = false;
     std::vector<double> phat(w.M);
     window_transform(p.poly, w.m, w.n, w.M, phat.data());
     cudaStream_t st = p.stream;
@@ -758,10 +807,15 @@ int compute_multipliers(Plan& p, int s)
         return ADDKER_ECUDA;
     }
     if (p.reg == ADDKER_REG_SEPARABLE) {
-        if (separable_coefficients(w.D, w.M, p.ell[s], p.eps_B, p.range, w.feat, fit, a, b, st) != cudaSuccess) {
+        if (separable_coefficients(w.D, w.M, p.ell[s], p.eps_B, p.range, w.feat, fit, a, b, cp, st) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(a);
             return ADDKER_ECUDA;
+        }
+        const int ds = decide_split(w.D, w.M, b, cp, st, &split);
+        if (ds != ADDKER_OK) {
+            cudaFree(a);
+            return ds;
         }
     } else {
         // radial reading: default degree M eps_B rounded half up, at least 1
@@ -788,13 +842,19 @@ int compute_multipliers(Plan& p, int s)
         }
     }
     float* mk[4] = {(float*)w.bK, (float*)w.bD, (float*)w.dconv, (float*)w.chat};
-    if (w.D == 1) k_multipliers<1><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, mk[0], mk[1], mk[2], mk[3]);
-    else if (w.D == 2) k_multipliers<2><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, mk[0], mk[1], mk[2], mk[3]);
-    else k_multipliers<3><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, mk[0], mk[1], mk[2], mk[3]);
+    const double* sub = split ? cp : nullptr;
+    if (w.D == 1) k_multipliers<1><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, mk[0], mk[1], mk[2], mk[3], sub);
+    else if (w.D == 2)
+        k_multipliers<2><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, mk[0], mk[1], mk[2], mk[3], sub);
+    else k_multipliers<3><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, mk[0], mk[1], mk[2], mk[3], sub);
     cudaError_t e = cudaGetLastError();
     cudaError_t e2 = cudaStreamSynchronize(st);
     cudaFree(a);
     if (e != cudaSuccess || e2 != cudaSuccess) return ADDKER_ECUDA;
+    p.pq[s] = split ? 1.0 / (2.0 * p.ell[s] * p.ell[s]) : 0.0;
+    w.pq = (float)p.pq[s];
+    p.any_split = false;
+    for (double q : p.pq) p.any_split = p.any_split || q != 0.0;
     return ADDKER_OK;
 }
 
@@ -1243,31 +1303,36 @@ void window_poly_for(int m, double sigma_os, WinPoly* poly)
 
 // Fourier multipliers bK, bD, dconv of window w (pointers already set) for length scale ell under the
 // separable reading (axis t is feature t of range: device, per-feature [min, max] of the window's
-// points), computed in the caller's FP64 scratch of at least 2 M^D + 4 M doubles. Enqueued on st and
-// waited for.
+// points), with the quadratic split decided as for a plan (*pq receives 1/(2 ell^2) or 0), computed in
+// the caller's FP64 scratch of at least 3 M^D + 6 M doubles. Enqueued on st and waited for.
 int multipliers_with_scratch(const WinDev& w, double ell, double eps_B, const float* range, const WinPoly& poly,
-                             double* scratch, cudaStream_t st)
+                             double* scratch, cudaStream_t st, float* pq)
 {
     int64_t total = 1;
     for (int t = 0; t < w.D; ++t) total *= w.M;
     double* a = scratch;
     double* b = a + total;
-    double* ph = b + total;
+    double* cp = b + total;
+    double* ph = cp + total;
     double* fit = ph + w.M;
     double phat[kMaxBandwidth];
     window_transform(poly, w.m, w.n, w.M, phat);
     CK(cudaMemcpyAsync(ph, phat, sizeof(double) * w.M, cudaMemcpyHostToDevice, st));
     const int feat[3] = {0, 1, 2};
-    CK(separable_coefficients(w.D, w.M, ell, eps_B, range, feat, fit, a, b, st));
+    CK(separable_coefficients(w.D, w.M, ell, eps_B, range, feat, fit, a, b, cp, st));
+    bool split = false;
+    CS(decide_split(w.D, w.M, b, cp, st, &split));
+    const double* sub = split ? cp : nullptr;
     const int th = 256, bl = grid_blocks(total, th);
     float* bK = const_cast<float*>(w.bK);
     float* bD = const_cast<float*>(w.bD);
     float* dc = const_cast<float*>(w.dconv);
-    if (w.D == 1) k_multipliers<1><<<bl, th, 0, st>>>(a, b, w.M, w.n, ph, bK, bD, dc, nullptr);
-    else if (w.D == 2) k_multipliers<2><<<bl, th, 0, st>>>(a, b, w.M, w.n, ph, bK, bD, dc, nullptr);
-    else k_multipliers<3><<<bl, th, 0, st>>>(a, b, w.M, w.n, ph, bK, bD, dc, nullptr);
+    if (w.D == 1) k_multipliers<1><<<bl, th, 0, st>>>(a, b, w.M, w.n, ph, bK, bD, dc, nullptr, sub);
+    else if (w.D == 2) k_multipliers<2><<<bl, th, 0, st>>>(a, b, w.M, w.n, ph, bK, bD, dc, nullptr, sub);
+    else k_multipliers<3><<<bl, th, 0, st>>>(a, b, w.M, w.n, ph, bK, bD, dc, nullptr, sub);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
+    *pq = split ? (float)(1.0 / (2.0 * ell * ell)) : 0.f;
     return ADDKER_OK;
 }
 
@@ -1414,7 +1479,22 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
     if (status == ADDKER_OK) status = dalloc(p, &p.wins_dev, P);
     if (status == ADDKER_OK) status = dalloc(p, &p.scale_dev, 3 * P);
     if (status == ADDKER_OK) status = dalloc(p, &p.dots, 2 * P);
-    if (status == ADDKER_OK) status = dalloc(p, &p.counters, 16);
+    if (status == ADDKER_OK) {
+        // the persistent kernels' counter (16 ints), then the moments: kMaxRhsChunk slots x P windows x 8,
+        // then P x 8 kept by addker_vjp
+        double* buf = nullptr;
+        status = dalloc(p, &buf, 8 + 8 * (int64_t)P * (kMaxRhsChunk + 1));
+        if (status == ADDKER_OK) {
+            p.counters = reinterpret_cast<int*>(buf);
+            p.mom = buf + 8;
+            p.mom_saved = p.mom + 8 * (int64_t)P * kMaxRhsChunk;
+            for (int s = 0; s < P; ++s) {
+                p.win[s].mom = p.mom + 8 * s;
+                p.win[s].mstride = 8 * (int64_t)P;
+            }
+        }
+    }
+    p.pq.assign(P, 0.0);
     for (int s = 0; s < P && status == ADDKER_OK; ++s) status = compute_multipliers(p, s);
     if (status == ADDKER_OK && cudaMemcpy(p.wins_dev, p.win.data(), sizeof(WinDev) * P, cudaMemcpyHostToDevice) != cudaSuccess)
         status = ADDKER_ECUDA;
@@ -1443,6 +1523,7 @@ int addker_set_params(addker_plan* plan, const double* ell, double sigma_f)
     CK(cudaStreamSynchronize(p.stream));
     clear_graphs(p);                               // sigma_f is baked into captured window sums
     for (int s = 0; s < p.P; ++s) CS(compute_multipliers(p, s));
+    CK(cudaMemcpy(p.wins_dev, p.win.data(), sizeof(WinDev) * p.P, cudaMemcpyHostToDevice));   // the split may change
     return upload_scales(p);
 }
 
@@ -1596,6 +1677,8 @@ int addker_vjp(addker_plan* plan, const float* v, const float* w, float* grad_v,
     for (int pass = 0; pass < 2; ++pass) {
         const float* u = pass == 0 ? w : v;
         CK(launch_spread(p, -1, u, p.N, 1, st, nullptr));         // slot 0; the transforms re-zero the grids
+        if (pass == 0 && p.any_split)                              // w's moments, before v's replace them
+            CK(cudaMemcpyAsync(p.mom_saved, p.mom, sizeof(double) * 8 * p.P, cudaMemcpyDeviceToDevice, st));
         CK(launch_transforms(p, -1, 1, st, nullptr, false));
         CK(launch_gather_grad(p, pass, pass == 0 ? v : w, ks, gx, st, nullptr));
         if (pass == 0) {
@@ -1608,9 +1691,13 @@ int addker_vjp(addker_plan* plan, const float* v, const float* w, float* grad_v,
         }
     }
     ThetaScale sc;
-    for (int s = 0; s < p.P; ++s) sc.s[s] = p.sigma_f * p.sigma_f * der_factor(p) / p.ell[s];
+    for (int s = 0; s < p.P; ++s) {
+        sc.s[s] = p.sigma_f * p.sigma_f * der_factor(p) / p.ell[s];
+        sc.q[s] = p.pq[s];
+    }
     sc.s[p.P] = 2.0 * p.sigma_f;
-    launch_k(true, k_theta_grad, dim3(1), dim3(64), 0, st, (const double*)p.dots, p.P, sc, grad_theta);
+    launch_k(true, k_theta_grad, dim3(1), dim3(64), 0, st, (const double*)p.dots, p.P, sc, (const double*)p.mom,
+             (const double*)p.mom_saved, grad_theta);
     CK(cudaGetLastError());
     return ADDKER_OK;
 }

@@ -68,6 +68,13 @@ struct WinDev {                          // copied by value into kernel paramete
     int64_t gsz, b1sz, b2sz;
     const float2* twf[3];                // [axis]: box[axis] x M
     const float2* twi[3];                // [axis]: M x box[axis]
+    // the quadratic split (a window whose derivative kernel's quadratic part ||r||^2/(2 ell^2) is
+    // evaluated through moments instead of the transforms): pq = 1/(2 ell^2) when split, else 0; the
+    // moments of right-hand side r are mom[r * mstride + c], c = 0 .. 4: sum v, sum x v, sum y v,
+    // sum z v, sum ||x||^2 v (over this window's coordinates; zeroed by every spread launch)
+    double* mom;
+    int64_t mstride;
+    float pq;
     int D, M, n, m;
     int feat[3];                         // feature (column of the points array) of each axis
     int lo[3];                           // grid-array index (l + n/2) of the box origin per axis
@@ -119,7 +126,13 @@ struct Plan {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
     int64_t launches[5] = {0, 0, 0, 0, 0};
     double* dots = nullptr;               // 2P doubles: gradient dot products (addker_vjp)
-    int* counters = nullptr;              // work counters of the persistent kernels (zeroed per launch)
+    int* counters = nullptr;              // work counters of the persistent kernels (16 ints), followed by
+                                          // the moments of the quadratic split: kMaxRhsChunk x P x 8 doubles
+                                          // (mom), then P x 8 saved by addker_vjp (mom_saved)
+    double* mom = nullptr;
+    double* mom_saved = nullptr;
+    bool any_split = false;               // some window's quadratic part is split off
+    std::vector<double> pq;               // per window: 1/(2 ell^2) when split, else 0 (FP64 copy of WinDev.pq)
     // CUDA graphs of repeated products (addker_set_graphs): a product whose arguments repeat those of
     // the previous call is captured once and replayed; any change of buffers or scalars clears them
     struct GraphKey {
@@ -227,6 +240,66 @@ __device__ __forceinline__ void window_weights(const WinPoly& P, float x, int n,
     for (int q = 0; q < W / 2; ++q) window_pair(P, q, u, u2, &w[q], &w[W - 1 - q]);
 }
 
+// The moments of the quadratic split, per lane: m[0] += v, m[1..D] += x_t v, m[4] += ||x||^2 v.
+template <int D>
+__device__ __forceinline__ void moments_add(float* m, float x, float y, float z, float v)
+{
+    m[0] += v;
+    m[1] = fmaf(x, v, m[1]);
+    if (D >= 2) m[2] = fmaf(y, v, m[2]);
+    if (D >= 3) m[3] = fmaf(z, v, m[3]);
+    float r2 = x * x;
+    if (D >= 2) r2 = fmaf(y, y, r2);
+    if (D >= 3) r2 = fmaf(z, z, r2);
+    m[4] = fmaf(r2, v, m[4]);
+}
+
+// Sum the five per-lane moments over the warp (every lane must call) and add them to dst in FP64: the
+// partial sums of one work item are short, so FP32 within the item and FP64 across items keep the totals
+// at FP32 accuracy relative to their own size.
+__device__ __forceinline__ void moments_flush(float* m, double* dst, int lane)
+{
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        float x = m[c];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0 && dst) atomicAdd(dst + c, (double)x);
+        m[c] = 0.f;
+    }
+}
+
+// The quadratic part of the derivative product at a target, pq (||x||^2 m0 - 2 x.m1 + m2), from the
+// moments of right-hand side r (zero for a window that is not split).
+struct Quad {
+    float q0, qx, qy, qz, q2;
+};
+__device__ __forceinline__ Quad quad_of(const WinDev& W, int r)
+{
+    Quad q = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (W.pq != 0.f) {
+        const double* m = W.mom + r * W.mstride;
+        const double a = (double)W.pq;
+        q.q0 = (float)(a * m[0]);
+        q.qx = (float)(-2.0 * a * m[1]);
+        q.qy = (float)(-2.0 * a * m[2]);
+        q.qz = (float)(-2.0 * a * m[3]);
+        q.q2 = (float)(a * m[4]);
+    }
+    return q;
+}
+template <int D>
+__device__ __forceinline__ float quad_eval(const Quad& q, float x, float y, float z)
+{
+    float r2 = x * x;
+    if (D >= 2) r2 = fmaf(y, y, r2);
+    if (D >= 3) r2 = fmaf(z, z, r2);
+    float t = fmaf(q.q0, r2, q.q2);
+    t = fmaf(q.qx, x, t);
+    if (D >= 2) t = fmaf(q.qy, y, t);
+    if (D >= 3) t = fmaf(q.qz, z, t);
+    return t;
+}
+
 // runtime W (generic kernels)
 __device__ __forceinline__ void window_weights_n(const WinPoly& P, float x, int n, int W, float* w, int* cell)
 {
@@ -302,7 +375,7 @@ int gsi_run(Plan& p, const float* v, int cap, int* feats, double* rho, double* t
 // Building blocks used without a plan (addker_fastsum_noalloc).
 void window_poly_for(int m, double sigma_os, WinPoly* poly);
 int multipliers_with_scratch(const WinDev& w, double ell, double eps_B, const float* range, const WinPoly& poly,
-                             double* scratch, cudaStream_t st);
+                             double* scratch, cudaStream_t st, float* pq);
 cudaError_t feature_range_async(const float* X, int64_t N, int d, float* range, int* bad, cudaStream_t st);
 cudaError_t twiddles_into(const WinDev& w, float2* const tw[3], cudaStream_t st);
 cudaError_t launch_transforms_window(const WinDev& w, const WinDev* w_dev, cudaStream_t st);

@@ -52,43 +52,73 @@ int scratch_for_current_device(unsigned char** out)
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Spreading, one thread per (unsorted) point, atomics into the full n^D grid. A point whose support
-// would leave the grid (outside the ball, or not finite) is skipped and raises *flag.
+// would leave the grid (outside the ball, or not finite) is skipped and raises *flag. With mom (not
+// NULL) the block also adds the moments of the quadratic split (sum v, sum x v, sum ||x||^2 v) to mom[0..5);
+// no thread leaves early, so the block's reductions see every lane.
 template <int D>
-__global__ void k_na_spread(const float* __restrict__ X, int64_t N, const float* __restrict__ v, float* grid,
-                            int n, int m, float rho2, const WinPoly poly, int* flag)
+__global__ void __launch_bounds__(128) k_na_spread(const float* __restrict__ X, int64_t N, const float* __restrict__ v,
+                                                   float* grid, int n, int m, float rho2, const WinPoly poly, int* flag,
+                                                   double* mom)
 {
+    __shared__ float part[4][5];
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= N) return;
     const int W = 2 * m;
     float w[3][kMaxW];
     int cell[3] = {0, 0, 0};
-    float r2 = 0.f;
-    for (int t = 0; t < D; ++t) r2 = fmaf(X[j * D + t], X[j * D + t], r2);
-    if (!(r2 <= rho2)) { atomicOr(flag, 1); return; }          // same ball as addker_setup checks
-    for (int t = 0; t < D; ++t) {
-        const float x = X[j * D + t];
-        if (!(fabsf(x) < 0.5f)) { atomicOr(flag, 1); return; }
-        window_weights_n(poly, x, n, W, w[t], &cell[t]);
-        if (cell[t] - m + 1 < 0 || cell[t] + m > n - 1) { atomicOr(flag, 1); return; }
+    float xs[3] = {0.f, 0.f, 0.f};
+    bool ok = j < N;
+    if (ok) {
+        float r2 = 0.f;
+        for (int t = 0; t < D; ++t) {
+            xs[t] = X[j * D + t];
+            r2 = fmaf(xs[t], xs[t], r2);
+        }
+        ok = r2 <= rho2;                                       // same ball as addker_setup checks
+        for (int t = 0; t < D && ok; ++t) {
+            ok = fabsf(xs[t]) < 0.5f;
+            if (!ok) break;
+            window_weights_n(poly, xs[t], n, W, w[t], &cell[t]);
+            ok = cell[t] - m + 1 >= 0 && cell[t] + m <= n - 1;
+        }
+        if (!ok) atomicOr(flag, 1);
     }
-    const float vj = v[j];
-    for (int a = 0; a < W; ++a) {
-        const int ia = cell[0] - m + 1 + a;
-        if (D == 1) { atomicAdd(grid + ia, vj * w[0][a]); continue; }
-        for (int b = 0; b < W; ++b) {
-            const int ib = cell[1] - m + 1 + b;
-            const float vab = vj * w[0][a] * w[1][b];
-            if (D == 2) { atomicAdd(grid + (size_t)ia * n + ib, vab); continue; }
-            float* row = grid + ((size_t)ia * n + ib) * n + (cell[2] - m + 1);
-            for (int c = 0; c < W; ++c) atomicAdd(row + c, vab * w[2][c]);
+    const float vj = ok ? v[j] : 0.f;
+    if (ok) {
+        for (int a = 0; a < W; ++a) {
+            const int ia = cell[0] - m + 1 + a;
+            if (D == 1) { atomicAdd(grid + ia, vj * w[0][a]); continue; }
+            for (int b = 0; b < W; ++b) {
+                const int ib = cell[1] - m + 1 + b;
+                const float vab = vj * w[0][a] * w[1][b];
+                if (D == 2) { atomicAdd(grid + (size_t)ia * n + ib, vab); continue; }
+                float* row = grid + ((size_t)ia * n + ib) * n + (cell[2] - m + 1);
+                for (int c = 0; c < W; ++c) atomicAdd(row + c, vab * w[2][c]);
+            }
+        }
+    }
+    if (mom) {                                                  // block-uniform
+        float mm[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        moments_add<D>(mm, xs[0], xs[1], xs[2], vj);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int c = 0; c < 5; ++c) {
+            float x = mm[c];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) part[warp][c] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x < 5) {
+            const float t = part[0][threadIdx.x] + part[1][threadIdx.x] + part[2][threadIdx.x] + part[3][threadIdx.x];
+            atomicAdd(mom + threadIdx.x, (double)t);
         }
     }
 }
 
 // Interpolation, one thread per point: Kv = sK f^K, dK = sD f^der.
+// A split window (pq != 0) adds pq (||x||^2 m0 - 2 x.m1 + m2) to the derivative product.
 template <int D>
 __global__ void k_na_gather(const float* __restrict__ X, int64_t N, const float2* __restrict__ h, int n, int m,
-                            const WinPoly poly, float sK, float sD, float* __restrict__ Kv, float* __restrict__ dK)
+                            const WinPoly poly, float sK, float sD, float* __restrict__ Kv, float* __restrict__ dK,
+                            const double* __restrict__ mom, float pq)
 {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= N) return;
@@ -126,7 +156,16 @@ __global__ void k_na_gather(const float* __restrict__ X, int64_t N, const float2
         fD = fmaf(uD, w[0][a], fD);
     }
     Kv[j] = sK * fK;
-    if (dK) dK[j] = sD * fD;
+    if (dK) {
+        float qd = 0.f;
+        if (pq != 0.f) {
+            const double a = (double)pq;
+            const Quad q = {(float)(a * mom[0]), (float)(-2.0 * a * mom[1]), (float)(-2.0 * a * mom[2]),
+                            (float)(-2.0 * a * mom[3]), (float)(a * mom[4])};
+            qd = quad_eval<D>(q, X[j * D], D >= 2 ? X[j * D + 1] : 0.f, D >= 3 ? X[j * D + 2] : 0.f);
+        }
+        dK[j] = sD * (fD + qd);
+    }
 }
 
 }  // namespace
@@ -157,7 +196,8 @@ extern "C" int addker_fastsum_noalloc(const float* points, int64_t N, int d, dou
     const size_t o_spec = off; off = align256(off + sizeof(float4) * md);
     const size_t o_mult = off; off = align256(off + sizeof(float) * 3 * md);
     const size_t o_tw = off;   off = align256(off + sizeof(float2) * 2 * (size_t)n * M * D);
-    const size_t o_coef = off; off = align256(off + sizeof(double) * (2 * md + 4 * M));
+    const size_t o_coef = off; off = align256(off + sizeof(double) * (3 * md + 6 * M));
+    const size_t o_mom = off;  off = align256(off + sizeof(double) * 8);
     const size_t o_win = off;  off = align256(off + sizeof(WinDev));
     const size_t o_flag = off; off = align256(off + sizeof(int));
     const size_t o_range = off; off = align256(off + sizeof(float) * 2 * 3 + sizeof(int));
@@ -198,6 +238,7 @@ extern "C" int addker_fastsum_noalloc(const float* points, int64_t N, int d, dou
     WinDev* w_dev = reinterpret_cast<WinDev*>(base + o_win);
     int* flag = reinterpret_cast<int*>(base + o_flag);
     float* range = reinterpret_cast<float*>(base + o_range);
+    double* mom = reinterpret_cast<double*>(base + o_mom);
     int* bad = reinterpret_cast<int*>(range + 2 * 3);
 
     WinPoly poly;
@@ -205,25 +246,29 @@ extern "C" int addker_fastsum_noalloc(const float* points, int64_t N, int d, dou
     // the array keeps the previous call's contents: clear the grid and the flag
     if (cudaMemsetAsync(w.grid, 0, sizeof(float) * nd, st) != cudaSuccess) return ADDKER_ECUDA;
     if (cudaMemsetAsync(flag, 0, sizeof(int), st) != cudaSuccess) return ADDKER_ECUDA;
+    if (cudaMemsetAsync(mom, 0, sizeof(double) * 8, st) != cudaSuccess) return ADDKER_ECUDA;
     if (cudaMemcpyAsync(w_dev, &w, sizeof(WinDev), cudaMemcpyHostToDevice, st) != cudaSuccess) return ADDKER_ECUDA;
     if (twiddles_into(w, tw, st) != cudaSuccess) return ADDKER_ECUDA;
     // the separable reading's fit intervals come from the points' largest |coordinate| per axis
     if (feature_range_async(points, N, D, range, bad, st) != cudaSuccess) return ADDKER_ECUDA;
-    const int mst = multipliers_with_scratch(w, ell, eps_B, range, poly, reinterpret_cast<double*>(base + o_coef), st);
+    float pq = 0.f;                                            // the quadratic split's weight, or 0
+    const int mst = multipliers_with_scratch(w, ell, eps_B, range, poly, reinterpret_cast<double*>(base + o_coef), st,
+                                             &pq);
     if (mst != ADDKER_OK) return mst;
+    double* mom_used = pq != 0.f ? mom : nullptr;
 
     const int th = 128, bl = (int)((N + th - 1) / th);
     const double rho = 0.25 - eps_B / 2.0;
     const float rho2 = (float)(rho * rho * (1.0 + 4e-6));
-    if (D == 1) k_na_spread<1><<<bl, th, 0, st>>>(points, N, v, w.grid, n, cutoff, rho2, poly, flag);
-    else if (D == 2) k_na_spread<2><<<bl, th, 0, st>>>(points, N, v, w.grid, n, cutoff, rho2, poly, flag);
-    else k_na_spread<3><<<bl, th, 0, st>>>(points, N, v, w.grid, n, cutoff, rho2, poly, flag);
+    if (D == 1) k_na_spread<1><<<bl, th, 0, st>>>(points, N, v, w.grid, n, cutoff, rho2, poly, flag, mom_used);
+    else if (D == 2) k_na_spread<2><<<bl, th, 0, st>>>(points, N, v, w.grid, n, cutoff, rho2, poly, flag, mom_used);
+    else k_na_spread<3><<<bl, th, 0, st>>>(points, N, v, w.grid, n, cutoff, rho2, poly, flag, mom_used);
     if (cudaGetLastError() != cudaSuccess) return ADDKER_ECUDA;
     if (launch_transforms_window(w, w_dev, st) != cudaSuccess) return ADDKER_ECUDA;
     const float sK = (float)(sigma_f * sigma_f), sD = (float)(sigma_f * sigma_f * 2.0 / ell);
-    if (D == 1) k_na_gather<1><<<bl, th, 0, st>>>(points, N, w.h, n, cutoff, poly, sK, sD, Kv, dKdell);
-    else if (D == 2) k_na_gather<2><<<bl, th, 0, st>>>(points, N, w.h, n, cutoff, poly, sK, sD, Kv, dKdell);
-    else k_na_gather<3><<<bl, th, 0, st>>>(points, N, w.h, n, cutoff, poly, sK, sD, Kv, dKdell);
+    if (D == 1) k_na_gather<1><<<bl, th, 0, st>>>(points, N, w.h, n, cutoff, poly, sK, sD, Kv, dKdell, mom, pq);
+    else if (D == 2) k_na_gather<2><<<bl, th, 0, st>>>(points, N, w.h, n, cutoff, poly, sK, sD, Kv, dKdell, mom, pq);
+    else k_na_gather<3><<<bl, th, 0, st>>>(points, N, w.h, n, cutoff, poly, sK, sD, Kv, dKdell, mom, pq);
     if (cudaGetLastError() != cudaSuccess) return ADDKER_ECUDA;
     int hflag = 0;
     if (cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return ADDKER_ECUDA;

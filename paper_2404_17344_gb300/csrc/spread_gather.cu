@@ -32,6 +32,43 @@ constexpr int kWarps = 4;                 // warps per block in the item kernels
 // float2 pairs and use __ffma2_rn.
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+// Running totals of the quadratic split's moments in the persistent spreads: a warp's consecutive units
+// mostly share (window, right-hand side), so their warp-summed FP32 moments are added into lane c's FP64
+// register (c < 5) and reach global memory only when that pair changes and when the warp finishes. One
+// flush per unit put five FP64 atomics per unit on the same few addresses, whose queue slowed the grid's
+// own atomic adds in the same L2 slices.
+struct MomAcc {
+    double a;
+    int key;                              // window * kMaxRhsChunk + rhs of the running total, or -1
+};
+__device__ __forceinline__ void mom_flush(const MomAcc& acc, const WinDev* __restrict__ wins, int lane)
+{
+    if (acc.key >= 0 && lane < 5) {
+        const WinDev& W = wins[acc.key / kMaxRhsChunk];
+        atomicAdd(W.mom + (acc.key % kMaxRhsChunk) * W.mstride + lane, acc.a);
+    }
+}
+// End of a unit of split window w, right-hand side r: fold the lanes' moments mm into the running total.
+__device__ __forceinline__ void mom_unit_end(MomAcc& acc, float* mm, const WinDev* __restrict__ wins, int w, int r,
+                                             int lane)
+{
+    float t = 0.f;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        float x = mm[c];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == c) t = x;
+        mm[c] = 0.f;
+    }
+    const int key = w * kMaxRhsChunk + r;
+    if (key != acc.key) {
+        mom_flush(acc, wins, lane);
+        acc.key = key;
+        acc.a = 0.0;
+    }
+    acc.a += (double)t;
+}
+
 // fast 3-D spread, m = 4 (W = 8)
 // Staged per point (STRIDE floats): x_a v [8] | y [8] | z [8]. The two half-warps take alternate
 // staged points (hw = lane >> 4). Within a half-warp, lane (ah, bh, cq) accumulates
@@ -78,6 +115,8 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_spread3_w8(const int4* __res
         pn = pts[lane];
         vn = __ldg(vr + __float_as_int(pn.w));
     }
+    float mm[5] = {0.f, 0.f, 0.f, 0.f, 0.f};      // moments of the quadratic split over this unit
+    MomAcc macc = {0.0, -1};
     while (true) {
         float2 acc[4][2][2];
 #pragma unroll
@@ -87,6 +126,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_spread3_w8(const int4* __res
         const int count = it.y;
         const int n = P->n;
         const bool more = un < nunits;
+        const bool split = P->pq != 0.f;
         for (int base = 0; base < count; base += 32) {
             const float4 p = pn;
             const float vv = vn;
@@ -104,6 +144,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_spread3_w8(const int4* __res
                 window_weights<W>(poly, p.z, n, wz, &cz);
 #pragma unroll
                 for (int q = 0; q < W; ++q) wx[q] *= vv;
+                if (split) moments_add<3>(mm, p.x, p.y, p.z, vv);
             } else {
 #pragma unroll
                 for (int q = 0; q < W; ++q) { wx[q] = 0.f; wy[q] = 0.f; wz[q] = 0.f; }
@@ -165,6 +206,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_spread3_w8(const int4* __res
             grid_add(g + oa + 2 * sy, ge ? ge + oa + 2 * sy : nullptr, acc[a][1][0].x);
             grid_add(g + oa + 3 * sy, ge ? ge + oa + 3 * sy : nullptr, acc[a][1][0].y);
         }
+        if (split) mom_unit_end(macc, mm, wins, it.w, r, lane);
         if (!more) break;
         // advance: the prefetched unit becomes current; take the one after it
         it = itn;
@@ -176,6 +218,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_spread3_w8(const int4* __res
         un = __shfl_sync(0xffffffffu, un, 0);
         itn = un < nunits ? items[un % nitems] : make_int4(0, 0, 0, 0);
     }
+    mom_flush(macc, wins, lane);
 }
 
 // Contraction of the staged box t4 with NP points per lane, p[i] written out where has[i]. The pair
@@ -184,7 +227,7 @@ template <int NP, bool WK, bool WD>
 __device__ __forceinline__ void gather_points(const float4* t4, const float4 (&p)[2], const bool (&has)[2], int n,
                                               const WinPoly& poly, float* __restrict__ outK,
                                               float* __restrict__ outD, float sK, float sD, int64_t offK,
-                                              int64_t offD)
+                                              int64_t offD, const Quad& Q)
 {
     constexpr int W = 8;
     float x[NP][W];
@@ -199,9 +242,11 @@ __device__ __forceinline__ void gather_points(const float4* t4, const float4 (&p
 #pragma unroll
         for (int q = 0; q < W; ++q) { y[i][q] = f2(a[q], a[q]); z[i][q] = f2(b[q], b[q]); }
     }
+    // (K, der) per point; the derivative's quadratic part (quadratic split, zero otherwise) starts its sum, so
+    // the moments' coefficients are not live through the contraction
     float2 f[NP];
 #pragma unroll
-    for (int i = 0; i < NP; ++i) f[i] = f2(0.f, 0.f);          // (K, der) per point
+    for (int i = 0; i < NP; ++i) f[i] = f2(0.f, WD ? quad_eval<3>(Q, p[i].x, p[i].y, p[i].z) : 0.f);
 #pragma unroll 1
     for (int a = 0; a < W; ++a) {
         float2 u[NP];
@@ -288,6 +333,7 @@ __device__ __forceinline__ void gather3_item(const int4 it, const WinDev& P, flo
     const float4* t4 = reinterpret_cast<const float4*>(t);
     const float sK = WK ? scaleK[it.w] : 0.f;
     const float sD = WD ? scaleD[it.w] : 0.f;
+    const Quad Q = WD ? quad_of(P, r) : Quad{0.f, 0.f, 0.f, 0.f, 0.f};
     const int n = P.n;
     // two points per lane while more than 32 remain, then one, so tail lanes do no dead work
     const int64_t offK = it.w * strideK + r * rstrideK, offD = it.w * strideD + r * rstrideD;
@@ -300,8 +346,8 @@ __device__ __forceinline__ void gather3_item(const int4 it, const WinDev& P, flo
             pa[0] = pts[min(nb + lane, count - 1)];
             pa[1] = pts[min(nb + 32 + lane, count - 1)];
         }
-        if (np == 2) gather_points<2, WK, WD>(t4, pc, has, n, poly, outK, outD, sK, sD, offK, offD);
-        else if (has[0]) gather_points<1, WK, WD>(t4, pc, has, n, poly, outK, outD, sK, sD, offK, offD);
+        if (np == 2) gather_points<2, WK, WD>(t4, pc, has, n, poly, outK, outD, sK, sD, offK, offD, Q);
+        else if (has[0]) gather_points<1, WK, WD>(t4, pc, has, n, poly, outK, outD, sK, sD, offK, offD, Q);
         base = nb;
     }
 }
@@ -369,6 +415,7 @@ __device__ __forceinline__ void spread_lowd_item(const int4 it, const WinDev& P,
     float acc[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.f;
+    float mm[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     // U points per lane per round, their loads issued together (the work per point is small, so one
     // point at a time would leave the loop waiting on memory); points past the item weigh 0
     constexpr int U = 4;
@@ -389,6 +436,7 @@ __device__ __forceinline__ void spread_lowd_item(const int4 it, const WinDev& P,
             float wx[W];
             int c;
             window_weights<W>(poly, pu.x, P.n, wx, &c);
+            moments_add<D>(mm, pu.x, pu.y, 0.f, vu);          // vu = 0 past the item's end
             if (D == 1) {
 #pragma unroll
                 for (int a = 0; a < W; ++a) acc[a] = fmaf(vu, wx[a], acc[a]);
@@ -409,6 +457,7 @@ __device__ __forceinline__ void spread_lowd_item(const int4 it, const WinDev& P,
             }
         }
     }
+    if (P.pq != 0.f) moments_flush(mm, P.mom + r * P.mstride, lane);
     int base, held;
     warp_transpose_reduce<NV>(acc, lane, &base, &held);
     const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff;
@@ -476,6 +525,8 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_spread_w8_all(const int4* __
     float4 pn = make_float4(0.f, 0.f, 0.f, 0.f);
     float vn = 0.f;
     bool primed = false;
+    float mm[5] = {0.f, 0.f, 0.f, 0.f, 0.f};      // moments of the quadratic split over this unit
+    MomAcc macc = {0.0, -1};
     while (true) {
         const bool more = un < nunits;
         if (P->D != 3) {
@@ -504,6 +555,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_spread_w8_all(const int4* __
             for (int q = 0; q < 4; ++q) acc[a][q >> 1][q & 1] = f2(0.f, 0.f);
         const int count = it.y;
         const int n = P->n;
+        const bool split = P->pq != 0.f;
         // the next unit is prefetched only if it is 3-D as well
         const bool n3 = more && wins[itn.w].D == 3;
         for (int base = 0; base < count; base += 32) {
@@ -523,6 +575,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_spread_w8_all(const int4* __
                 window_weights<W>(poly, p.z, n, wz, &cz);
 #pragma unroll
                 for (int q = 0; q < W; ++q) wx[q] *= vv;
+                if (split) moments_add<3>(mm, p.x, p.y, p.z, vv);
             } else {
 #pragma unroll
                 for (int q = 0; q < W; ++q) { wx[q] = 0.f; wy[q] = 0.f; wz[q] = 0.f; }
@@ -584,6 +637,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_spread_w8_all(const int4* __
             grid_add(g + oa + 2 * sy, ge ? ge + oa + 2 * sy : nullptr, acc[a][1][0].x);
             grid_add(g + oa + 3 * sy, ge ? ge + oa + 3 * sy : nullptr, acc[a][1][0].y);
         }
+        if (split) mom_unit_end(macc, mm, wins, it.w, r, lane);
         primed = n3;
         if (!more) break;
         // advance: the prefetched unit becomes current; take the one after it
@@ -596,6 +650,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_spread_w8_all(const int4* __
         un = __shfl_sync(0xffffffffu, un, 0);
         itn = un < nunits ? items[(un % nitems + rot) % nitems] : make_int4(0, 0, 0, 0);
     }
+    mom_flush(macc, wins, lane);
 }
 
 // One 1-D or 2-D item (m = 4) by one warp; t holds at least (2m)^D entries.
@@ -621,6 +676,7 @@ __device__ __forceinline__ void gather_lowd_item(const int4 it, const WinDev& P,
     const float4* __restrict__ pts = P.pts + it.x;
     const float sK = WK ? scaleK[it.w] : 0.f;
     const float sD = WD ? scaleD[it.w] : 0.f;
+    const Quad Q = WD ? quad_of(P, r) : Quad{0.f, 0.f, 0.f, 0.f, 0.f};
     constexpr int U = 4;                                       // points per lane per round, loads together
     for (int k0 = lane; k0 < it.y; k0 += 32 * U) {
         float4 pp[U];
@@ -636,7 +692,7 @@ __device__ __forceinline__ void gather_lowd_item(const int4 it, const WinDev& P,
             float wx[W];
             int c;
             window_weights<W>(poly, p.x, P.n, wx, &c);
-            float2 f = make_float2(0.f, 0.f);
+            float2 f = make_float2(0.f, WD ? quad_eval<D>(Q, p.x, p.y, 0.f) : 0.f);
             if (D == 1) {
 #pragma unroll
                 for (int a = 0; a < W; ++a) f = __ffma2_rn(t[a], make_float2(wx[a], wx[a]), f);
@@ -714,9 +770,11 @@ __global__ void __launch_bounds__(128) k_spread_generic(const int4* __restrict__
     if (D >= 3) WD *= W;
     for (int i = threadIdx.x; i < WD; i += blockDim.x) box[i] = 0.f;
     __syncthreads();
+    float mm[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     for (int k = threadIdx.x; k < it.y; k += blockDim.x) {
         const float4 p = P.pts[it.x + k];
         const float vv = __ldg(v + __float_as_int(p.w));
+        moments_add<D>(mm, p.x, p.y, p.z, vv);
         float w0[kMaxW], w1[kMaxW], w2[kMaxW];
         int c;
         window_weights_n(poly, p.x, P.n, W, w0, &c);
@@ -732,6 +790,7 @@ __global__ void __launch_bounds__(128) k_spread_generic(const int4* __restrict__
             }
         }
     }
+    if (P.pq != 0.f) moments_flush(mm, P.mom + r * P.mstride, threadIdx.x & 31);
     __syncthreads();
     const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff, cz = (it.z >> 16) & 0xff;
     const int ox = cx - P.m + 1 - P.lo[0], oy = cy - P.m + 1 - P.lo[1], oz = cz - P.m + 1 - P.lo[2];
@@ -760,6 +819,7 @@ __global__ void __launch_bounds__(128) k_gather_generic(const int4* __restrict__
     const float2* __restrict__ h = P.h + r * P.gsz;
     const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff, cz = (it.z >> 16) & 0xff;
     const int ox = cx - P.m + 1 - P.lo[0], oy = cy - P.m + 1 - P.lo[1], oz = cz - P.m + 1 - P.lo[2];
+    const Quad Q = WD ? quad_of(P, r) : Quad{0.f, 0.f, 0.f, 0.f, 0.f};
     for (int k = threadIdx.x; k < it.y; k += blockDim.x) {
         const float4 p = P.pts[it.x + k];
         float w0[kMaxW], w1[kMaxW], w2[kMaxW];
@@ -789,7 +849,7 @@ __global__ void __launch_bounds__(128) k_gather_generic(const int4* __restrict__
         }
         const int64_t i = (int64_t)__float_as_int(p.w);
         if (WK) outK[i + it.w * strideK + r * rstrideK] = scaleK[it.w] * fK;
-        if (WD) outD[i + it.w * strideD + r * rstrideD] = scaleD[it.w] * fD;
+        if (WD) outD[i + it.w * strideD + r * rstrideD] = scaleD[it.w] * (fD + quad_eval<D>(Q, p.x, p.y, p.z));
     }
 }
 
@@ -831,6 +891,10 @@ cudaError_t launch_spread(const Plan& p, int window, const float* v, int64_t ldv
     int launched = 0;
     const WinDev* wd = p.wins_dev;
     int k0 = 0;
+    // the persistent kernels' work counter and, when a window is split, the moments of these right-hand
+    // sides (they lie right after the counter: one memset)
+    const size_t zero = 16 * sizeof(int) + (p.any_split ? sizeof(double) * 8 * p.P * (size_t)nrhs : 0);
+    if (cudaMemsetAsync(p.counters, 0, zero, st) != cudaSuccess) return cudaGetLastError();
     if (window < 0) {
         // the m = 4 kinds (3-D, 1-D, 2-D fast) lie next to each other in the spread list: one persistent
         // launch for all of them, units taken from a zeroed counter
@@ -838,7 +902,6 @@ cudaError_t launch_spread(const Plan& p, int window, const float* v, int64_t ldv
         const int n3 = p.item_begin_sp[kKindFast3].back() - lo;
         if (hi > lo) {
             const int n = hi - lo, units = n * nrhs;
-            if (cudaMemsetAsync(p.counters, 0, sizeof(int), st) != cudaSuccess) return cudaGetLastError();
             if (n3 == n) {                    // 3-D items only: the kernel without the per-unit branch
                 const int nb = std::min(resident_blocks(k_spread3_w8, kWarps * 32), (units + kWarps - 1) / kWarps);
                 launch_k(false, k_spread3_w8, dim3(nb), dim3(kWarps * 32), 0, st, p.items + lo, n, units, p.counters,
@@ -866,7 +929,6 @@ cudaError_t launch_spread(const Plan& p, int window, const float* v, int64_t ldv
                 // persistent: as many blocks as fit at once, units taken from a zeroed counter
                 const int units = n * nrhs;
                 const int nb = std::min(resident_blocks(k_spread3_w8, kWarps * 32), (units + kWarps - 1) / kWarps);
-                if (cudaMemsetAsync(p.counters, 0, sizeof(int), st) != cudaSuccess) return cudaGetLastError();
                 launch_k(pdl, k_spread3_w8, dim3(nb), T, 0, st, it, n, units, p.counters, wd, v, ldv, p.poly);
                 break;
             }
