@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import workloads
-from oracle import gp
+from oracle import fastsum, gp
 
 
 def small(N=120, seed=5):
@@ -138,3 +138,77 @@ def test_planted_gradient_mistakes_are_caught(monkeypatch):
          for D in real(K, dK, wl.sigma_f)],
         [np.trace(np.linalg.solve(K + 0.3 * np.eye(wl.N), D)) for D in real(K, dK, wl.sigma_f)])])
     assert not np.allclose(g_flip, good, rtol=1e-3)
+
+
+# ---------------------------------------------------------------- preconditioned CG ----
+
+def test_woodbury_apply_is_the_dense_inverse():
+    rng = np.random.default_rng(21)
+    U = rng.standard_normal((80, 7))
+    w = rng.uniform(0.5, 3.0, 7)
+    beta = 0.03
+    r = rng.standard_normal((80, 2))
+    B = beta * np.eye(80) + U @ np.diag(w) @ U.T
+    np.testing.assert_allclose(gp.woodbury_apply(U, w, beta)(r), np.linalg.solve(B, r), rtol=1e-9, atol=1e-9)
+
+
+def test_fourier_basis_is_the_trig_sum_of_the_retained_modes():
+    """U diag(w) U^T equals sigma_f^2 sum over the retained (window, +-k) of c_hat_k e^{2 pi i k.(x_i - x_j)},
+    the constant mode counted once per window (cos(a - b) = cos a cos b + sin a sin b)."""
+    wl = workloads.tiny(N=40, d=5, windows=[(0, 1, 2), (3, 4)], ell=[0.3, 0.6])
+    X = wl.points.astype(np.float64)
+    coefs = [fastsum.coefficients_for(np.ascontiguousarray(X[:, list(w)]), wl.ell[s], 16)[0]
+             for s, w in enumerate(wl.windows)]
+    beta, sf = 1e-3, 1.3
+    modes, wmode = gp.fourier_modes(wl.windows, coefs, 1, beta, sf, 40)
+    U, owner = gp.fourier_basis(wl.points, wl.windows, modes)
+    got = U @ np.diag(wmode[owner]) @ U.T
+    want = np.zeros((40, 40))
+    for s, w in enumerate(wl.windows):
+        c = coefs[s]
+        M = c.shape[0]
+        xs = X[:, list(w)]
+        for k in np.ndindex(*c.shape):
+            kk = np.array(k) - M // 2
+            keep = np.all(kk == 0) or (s, tuple(kk)) in modes or (s, tuple(-kk)) in modes
+            if keep:
+                ph = 2 * np.pi * (xs @ kk)
+                want += sf ** 2 * c[k] * np.cos(ph[:, None] - ph[None, :])
+    np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-10)
+    assert len(modes) > 1 and all(wm > 0 for wm in wmode)
+
+
+def test_pcg_with_identity_is_cg():
+    rng = np.random.default_rng(22)
+    Q = rng.standard_normal((60, 60))
+    A = Q @ Q.T + 0.5 * np.eye(60)
+    y = rng.standard_normal(60)
+    x1, it1, r1 = gp.cg(lambda v: A @ v, y, 1e-10, 500)
+    x2, it2, r2 = gp.pcg(lambda v: A @ v, lambda v: v, y, 1e-10, 500)
+    # with M = I the flexible and the classical direction updates agree in exact arithmetic; in FP64 the
+    # iteration counts may differ by one
+    assert abs(it1 - it2) <= 2 and r2 <= 1e-10
+    np.testing.assert_allclose(x1, x2, rtol=1e-8, atol=1e-10)
+
+
+def test_fourier_preconditioner_on_the_gp_configuration():
+    """The GP configuration's points (a 1500-point sample, 8 windows of 3, ell = 0.5) at the configuration's
+    noise variance beta = 0.01: preconditioned CG reaches the dense solution in a fraction of plain CG's
+    iterations."""
+    wl = workloads.make("c4", N=2_000_000)
+    idx = np.random.default_rng(23).choice(wl.N, 1500, replace=False)
+    X = wl.points[idx]
+    y = wl.targets()[idx].astype(np.float64)
+    K, _ = gp.dense_kernel(X, wl.windows, wl.ell, wl.sigma_f)
+    beta = 0.01
+    A = K + beta * np.eye(len(y))
+    x_ref = np.linalg.solve(A, y)
+    coefs = [fastsum.coefficients_for(np.ascontiguousarray(wl.points[:, list(w)].astype(np.float64)), wl.ell[s], 32)[0]
+             for s, w in enumerate(wl.windows)]
+    modes, wmode = gp.fourier_modes(wl.windows, coefs, 1, beta, wl.sigma_f, len(y))
+    U, owner = gp.fourier_basis(X, wl.windows, modes)
+    Minv = gp.woodbury_apply(U, wmode[owner], beta)
+    xp, itp, rp = gp.pcg(lambda v: A @ v, Minv, y, 1e-8, 500)
+    xc, itc, rc = gp.cg(lambda v: A @ v, y, 1e-8, 2000)
+    assert rp <= 1e-8 and np.linalg.norm(xp - x_ref) <= 1e-5 * np.linalg.norm(x_ref)
+    assert itp * 3 < itc
