@@ -466,9 +466,11 @@ def run_gp(args, rank, world, local_rank):
     plus N(0, 0.01) noise; one step = one gradient of the GP log marginal likelihood in
     (ell_1..ell_8, sigma_f, beta): CG on (K + beta I) with 1 + 16 right-hand sides
     [y, z_1..z_16] (Rademacher probes, Hutchinson) to relative residual 1e-6, or at most --maxit
-    iterations (unpreconditioned CG on this system at N = 2e6 needs far more than fit in a benchmark
-    step, so the default caps it and reports the residual reached), then one fused product on
-    [alpha, z_1..z_16]."""
+    iterations, preconditioned with every window's lowest Fourier modes (--precond band; 0 = plain CG),
+    then one fused product on [alpha, z_1..z_16]. At the configuration's beta = 0.01 the FP32 operator's
+    error (~1e-7 ||K||, ||K|| ~ 1.6e7) is far above beta, so the solve stalls at a relative residual of a
+    few 1e-2 whatever the iteration count; the line reports the residual reached, measured with one more
+    product."""
     import numpy as np
     torch, dev, gpu_id = _setup_secondary(args, local_rank)
     import workloads
@@ -477,6 +479,7 @@ def run_gp(args, rank, world, local_rank):
     m = args.nrhs - 1
     wl = workloads.make("c4", N=N)
     op = AddKer(torch.from_numpy(wl.points).to(dev), wl.windows, wl.ell, wl.sigma_f, wl.bandwidth, wl.cutoff)
+    op.set_precond(args.precond)
     y = torch.from_numpy(wl.targets()).to(dev)
     Z = torch.from_numpy(wl.probes(m)).to(dev)
     beta, tol = args.beta, args.tol
@@ -504,7 +507,7 @@ def run_gp(args, rank, world, local_rank):
            "config": {"workload": f"c4-shaped at N={N}: d=24, correlated Gaussian features, 8 windows of 3, ell=0.5, "
                                   "M=32, m=4; y = 16-term random Fourier features per window + N(0, 0.01) noise",
                       "N": N, "probes": m, "beta": beta, "cg_tol": tol, "cg_maxit": args.maxit, "cg_iters": its,
-                      "alpha_relres": relres,
+                      "precond_band": args.precond, "alpha_relres": relres,
                       "ms_per_cg_iteration": ms / max(1, statistics.mean(its))},
            "grad": list(map(float, g)), "fit": fit, "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
@@ -552,9 +555,9 @@ def main():
                          "gp: one GP gradient (CG + Hutchinson) per step; cpu: FP64 oracle timings on the host "
                          "cores (no GPU)")
     ap.add_argument("--nrhs", type=int, default=64, help="right-hand sides per step (batched), 1 + probes (gp)")
-    ap.add_argument("--beta", type=float, default=1.0,
-                    help="gp: regularisation beta; the configuration's noise variance 0.01 leaves unpreconditioned "
-                         "FP32 CG without convergence at N = 2e6")
+    ap.add_argument("--beta", type=float, default=0.01,
+                    help="gp: regularisation beta (the configuration's noise variance 0.01)")
+    ap.add_argument("--precond", type=int, default=1, help="gp: preconditioner band (0 = plain CG)")
     ap.add_argument("--tol", type=float, default=1e-6, help="gp: CG relative residual tolerance")
     ap.add_argument("--maxit", type=int, default=100, help="gp: CG iterations at most")
     args = ap.parse_args()

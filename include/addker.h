@@ -23,7 +23,7 @@
  *
  * Entry points:
  *   plan         addker_opts_default, addker_setup, addker_set_params, addker_set_stream,
- *                addker_set_graphs, addker_autotune, addker_free, addker_info
+ *                addker_set_graphs, addker_set_precond, addker_autotune, addker_free, addker_info
  *   products     addker_matvec, addker_dmatvec, addker_matvec_all (device buffers),
  *                addker_matvec_all_host (host buffers), addker_fastsum_noalloc (no plan)
  *   gradients    addker_vjp (w^T K v with respect to v, ell, sigma_f and the points)
@@ -204,7 +204,7 @@ int addker_autotune(addker_plan* plan, const float* v, int nrhs, int* chosen, do
 /*
  * Conjugate gradients for the regression system (K + beta I) x = y (Sec. 3.3, eq. "regression_system";
  * the paper solves it with unpreconditioned CG to a relative residual tolerance), for nrhs independent
- * columns at once.
+ * columns at once; preconditioned by default (addker_set_precond).
  *   beta    regularisation (>= 0; K + beta I must be positive definite)
  *   y       device, N x nrhs float32, column-major (column j at y + j N)
  *   x       device, N x nrhs float32: the initial guess in, the solution out
@@ -218,6 +218,22 @@ int addker_autotune(addker_plan* plan, const float* v, int nrhs, int* chosen, do
  */
 int addker_cg(addker_plan* plan, double beta, const float* y, float* x, int nrhs, double tol, int maxit,
               int* iters, double* relres);
+
+/*
+ * Preconditioner of addker_cg and addker_gp_grad (not in the paper, which uses plain CG). At a small beta
+ * the regression system is ill-conditioned (condition number ~ N / beta for a kernel wide against the
+ * data): K's large eigenvalues belong to every window's lowest Fourier modes (Sec. 3.1: the even
+ * coefficients give each pair +-k the term 2 c_hat_k [cos(2 pi k.x) cos(2 pi k.x') + sin sin]). The
+ * preconditioner B = beta I + U W U^T keeps, for every window, the modes |k|_inf <= band whose weight
+ * sigma_f^2 2 c_hat_k times N is at least beta (plus the shared constant mode, weight sigma_f^2 sum_s c_hat_0),
+ * U = their cosines and sines at the points (N x r, at most 1024 columns; FP32), and applies B^{-1} by the
+ * Woodbury identity with U^T U accumulated in FP64 and factored by FP64 Cholesky. It is built on the first
+ * solve for a given beta (about 0.1 s and 4 N r bytes of device memory at N = 2e6) and kept until the
+ * hyperparameters, beta or this setting change; CG then runs the flexible (Polak-Ribiere) preconditioned
+ * iteration. band 0 gives plain CG; 1 (the default) to 3. If no mode qualifies or the factorisation fails,
+ * plain CG runs. EINVAL for band outside 0..3. Synchronises the plan's stream.
+ */
+int addker_set_precond(addker_plan* plan, int band);
 
 /*
  * Gradient of the GP log marginal likelihood L = -1/2 y^T A^{-1} y - 1/2 log det A - N/2 log 2 pi,

@@ -206,6 +206,11 @@ class AddKer:
         """Replay repeated identical products as CUDA graphs (default on); False launches every kernel."""
         native.check(self._ready().addker_set_graphs(self._plan, 1 if enable else 0), "addker_set_graphs")
 
+    def set_precond(self, band):
+        """CG preconditioner with every window's Fourier modes |k|_inf <= band (addker_set_precond; 0 = plain CG,
+        default 1)."""
+        native.check(self._ready().addker_set_precond(self._plan, int(band)), "addker_set_precond")
+
     def cg(self, y, beta, tol=1e-3, maxit=1000, x0=None):
         """Solve (K + beta I) x = y by conjugate gradients (addker_cg). y is (N,) or (N, nrhs); returns
         (x shaped like y, iterations per column, relative residual per column)."""

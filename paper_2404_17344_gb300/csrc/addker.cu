@@ -70,6 +70,7 @@ void clear_graphs(Plan& p)
 void release(Plan& p)
 {
     clear_graphs(p);
+    pc_release(p);
     if (p.cap_stream) cudaStreamDestroy(p.cap_stream);
     p.cap_stream = nullptr;
     if (p.copy_stream) cudaStreamDestroy(p.copy_stream);
@@ -849,8 +850,32 @@ int compute_multipliers(Plan& p, int s)
     else k_multipliers<3><<<bl, th, 0, st>>>(src[0], src[1], w.M, w.n, ph, mk[0], mk[1], mk[2], mk[3], sub);
     cudaError_t e = cudaGetLastError();
     cudaError_t e2 = cudaStreamSynchronize(st);
+    // the lowest modes' coefficients (FP64) for the CG preconditioner
+    std::vector<double> all(total);
+    cudaError_t e3 = e == cudaSuccess && e2 == cudaSuccess
+                         ? cudaMemcpy(all.data(), src[0], sizeof(double) * total, cudaMemcpyDeviceToHost)
+                         : cudaSuccess;
     cudaFree(a);
-    if (e != cudaSuccess || e2 != cudaSuccess) return ADDKER_ECUDA;
+    if (e != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return ADDKER_ECUDA;
+    {
+        const int B = 2 * kPcMaxBand + 1;
+        int64_t nb = 1;
+        for (int t = 0; t < w.D; ++t) nb *= B;
+        std::vector<double>& lc = p.lowc[s];
+        lc.assign(nb, 0.0);
+        for (int64_t o = 0; o < nb; ++o) {
+            int64_t rem = o, src_idx = 0, mult = 1;
+            bool inside = true;
+            for (int t = w.D - 1; t >= 0; --t) {
+                const int k = (int)(rem % B) - kPcMaxBand;
+                rem /= B;
+                if (k <= -w.M / 2 || k >= w.M / 2) inside = false;
+                src_idx += (int64_t)(k + w.M / 2) * mult;
+                mult *= w.M;
+            }
+            if (inside) lc[o] = all[src_idx];
+        }
+    }
     p.pq[s] = split ? 1.0 / (2.0 * p.ell[s] * p.ell[s]) : 0.0;
     w.pq = (float)p.pq[s];
     p.any_split = false;
@@ -1495,6 +1520,7 @@ int addker_setup(addker_plan** out, const float* points, int64_t N, int d, const
         }
     }
     p.pq.assign(P, 0.0);
+    p.lowc.assign(P, {});
     for (int s = 0; s < P && status == ADDKER_OK; ++s) status = compute_multipliers(p, s);
     if (status == ADDKER_OK && cudaMemcpy(p.wins_dev, p.win.data(), sizeof(WinDev) * P, cudaMemcpyHostToDevice) != cudaSuccess)
         status = ADDKER_ECUDA;
@@ -1522,9 +1548,20 @@ int addker_set_params(addker_plan* plan, const double* ell, double sigma_f)
     p.sigma_f = sigma_f;
     CK(cudaStreamSynchronize(p.stream));
     clear_graphs(p);                               // sigma_f is baked into captured window sums
+    pc_release(p);                                 // the preconditioner's modes and weights change
     for (int s = 0; s < p.P; ++s) CS(compute_multipliers(p, s));
     CK(cudaMemcpy(p.wins_dev, p.win.data(), sizeof(WinDev) * p.P, cudaMemcpyHostToDevice));   // the split may change
     return upload_scales(p);
+}
+
+int addker_set_precond(addker_plan* plan, int band)
+{
+    if (!plan || band < 0 || band > kPcMaxBand) return ADDKER_EINVAL;
+    Plan& p = plan->p;
+    CK(cudaStreamSynchronize(p.stream));
+    pc_release(p);
+    p.pc_band = band;
+    return ADDKER_OK;
 }
 
 int addker_set_graphs(addker_plan* plan, int enable)

@@ -31,6 +31,7 @@ inline int kind_of(int D, int m) { return m == 4 ? (D == 3 ? kKindFast3 : D) : 2
 constexpr int kItemPoints = 256;        // default points per work item (one warp); see build_items
 constexpr int kLowdChunkFactor = 8;     // spread items of 2-D windows hold this many times more points
 constexpr int kMaxBandwidth = 64;
+constexpr int kPcMaxBand = 3;           // largest |k|_inf of the CG preconditioner's Fourier modes
 
 // Piecewise polynomial form of the window used by every spreading/interpolation kernel: for a
 // coordinate with fractional grid offset frac = n x - floor(n x) in [0, 1) and u = 2 frac - 1, the
@@ -133,6 +134,16 @@ struct Plan {
     double* mom_saved = nullptr;
     bool any_split = false;               // some window's quadratic part is split off
     std::vector<double> pq;               // per window: 1/(2 ell^2) when split, else 0 (FP64 copy of WinDev.pq)
+    // the CG preconditioner (solver.cu): every window's lowest Fourier modes |k|_inf <= pc_band
+    int pc_band = 1;                      // addker_set_precond; 0 = plain CG
+    std::vector<std::vector<double>> lowc;  // per window: c_hat_k (FP64) for |k|_inf <= kPcMaxBand, index
+                                            // sum_t (k_t + kPcMaxBand) (2 kPcMaxBand + 1)^(D-1-t)
+    float* pc_U = nullptr;                // N x r basis (column-major), built on the first preconditioned solve
+    double* pc_G = nullptr;               // U^T U (r x r)
+    double* pc_L = nullptr;               // Cholesky factor of beta W^{-1} + U^T U for pc_beta (r x r)
+    double* pc_w = nullptr;               // r column weights (device)
+    int pc_r = 0;
+    double pc_beta = -1.0;
     // CUDA graphs of repeated products (addker_set_graphs): a product whose arguments repeat those of
     // the previous call is captured once and replayed; any change of buffers or scalars clears them
     struct GraphKey {
@@ -368,6 +379,9 @@ int cg_solve(Plan& p, double beta, const float* Y, float* X, int nrhs, double to
              double* relres);
 int gp_grad(Plan& p, double beta, const float* y, const float* Z, int m, double tol, int maxit, double* grad,
             double* fit, float* alpha_out, int* iters);
+
+// The CG preconditioner's device buffers (solver.cu): released here and rebuilt on the next solve.
+void pc_release(Plan& p);
 
 // Global sensitivity indices (gsi.cu): returns the number of feature subsets (or a negative status).
 int gsi_run(Plan& p, const float* v, int cap, int* feats, double* rho, double* total);

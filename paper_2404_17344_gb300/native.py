@@ -48,6 +48,7 @@ SIGNATURES = {
     "addker_set_params": (_I, [_VP, _VP, _D]),
     "addker_set_stream": (_I, [_VP, _VP]),
     "addker_set_graphs": (_I, [_VP, _I]),
+    "addker_set_precond": (_I, [_VP, _I]),
     "addker_autotune": (_I, [_VP, _VP, _I, _VP, _VP, _I]),
     "addker_gsi": (_I, [_VP, _VP, _I, _VP, _VP, _VP]),
     "addker_cg": (_I, [_VP, ctypes.c_double, _VP, _VP, _I, ctypes.c_double, _I, _VP, _VP]),
