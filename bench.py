@@ -453,7 +453,9 @@ def run_batched(args, rank, world, local_rank):
            "config": {"workload": f"c3-shaped at N={N}: d=15, windows 3,3,3,2,2,1,1, ell log-U[0.1,2], M=32/16, "
                                   f"m=4, U[-1,1] features scaled into the ball, {R} right-hand sides per step",
                       "N": N, "nrhs": R, "chunk": chunk, "chunk_spread": op.info()["chunk_spread"],
-                      "autotune_ms": tune_ms, "autotune_spread_ms": op.autotune_spread_times},
+                      "autotune_ms": tune_ms, "autotune_spread_ms": op.autotune_spread_times,
+                      "spread_blocks_per_sm": op.info()["spread_blocks_per_sm"],
+                      "autotune_residency_ms": {str(k): v for k, v in op.autotune_residency_times.items()}},
            "per_rhs_ms": ms / R, "single_rhs_ms": single_ms, "speedup_per_solve_vs_single": single_ms / (ms / R),
            "clocks": clk.summary(), "accuracy": acc, "plan": {k: v for k, v in op.info().items() if k != "windows"}}
     print(json.dumps(out), flush=True)

@@ -187,17 +187,19 @@ int addker_set_params(addker_plan* plan, const double* ell, double sigma_f);
 int addker_set_graphs(addker_plan* plan, int enable);
 
 /*
- * Autotuning of the work-item sizes: the spread and gather kernels take the points of each non-empty
- * grid cell in work items of at most `chunk` points (default 256 for both lists), their scheduling
- * grain. This call times the fused product (addker_matvec_all semantics) on v (device, N x nrhs,
- * column-major), one warm-up and three timed products per candidate, without graphs: first one size
- * for both kernels, chunk in {64, 128, 256, 512, 1024}; then, with the gather's size fixed at the
- * fastest, the spread's size over the same candidates. The fastest pair is kept for later products;
- * chosen (host, may be NULL) receives the gather's size (the spread's is addker_info's last value) and
- * times (host, may be NULL) up to `cap` milliseconds per product: the five joint candidates, then the
- * five spread candidates. Allocates and frees its own output buffers; synchronous on the plan's
- * stream. The paper has no counterpart (its library runs on the CPU): this is a scheduling choice of
- * the GPU path.
+ * Autotuning of the spread and gather schedules. The spread and gather kernels take the points of each
+ * non-empty grid cell in work items of at most `chunk` points (default 256 for both lists), their
+ * scheduling grain, and the persistent spread runs as many blocks per SM as fit. This call times the
+ * fused product (addker_matvec_all semantics) on v (device, N x nrhs, column-major), one warm-up and
+ * three timed products per candidate, without graphs: first one item size for both kernels, chunk in
+ * {64, 128, 256, 512, 1024}; then, with the gather's size fixed at the fastest, the spread's size over the
+ * same candidates; then the persistent spread's residency, 1, 2 or 3 blocks per SM or as many as fit
+ * (fewer resident warps contend less for the grid's atomic adds, more hide more latency). The fastest
+ * setting is kept for later products; chosen (host, may be NULL) receives the gather's size (the spread's
+ * and the residency are addker_info's last two values) and times (host, may be NULL) up to `cap`
+ * milliseconds per product: the five joint candidates, the five spread candidates, then the four
+ * residencies. Allocates and frees its own output buffers; synchronous on the plan's stream. The paper has
+ * no counterpart (its library runs on the CPU): these are scheduling choices of the GPU path.
  */
 int addker_autotune(addker_plan* plan, const float* v, int nrhs, int* chosen, double* times, int cap);
 
@@ -378,7 +380,8 @@ int addker_prescale_cube(const float* X, int64_t N, int d, const int* win_off, c
  *   then per window s: [4+4s] d_s  [5+4s] M_s  [6+4s] n_s  [7+4s] number of non-empty cells,
  *   then [4+4P] right-hand-side slots allocated  [5+4P] captured product graphs held
  *   [6+4P] product graph replays so far  [7+4P] points per gather work item at most
- *   [8+4P] points per spread work item at most (x8 for 2-D windows).
+ *   [8+4P] points per spread work item at most (x8 for 2-D windows)
+ *   [9+4P] blocks per SM of the persistent spread (0: as many as fit).
  * Returns the number of values available.
  */
 int addker_info(const addker_plan* plan, int64_t* info, int cap);

@@ -271,16 +271,19 @@ class AddKer:
 
     def autotune(self, v):
         """Time the fused product on v ((N,) or (N, nrhs)) for each work-item size in AUTOTUNE_CHUNKS (one
-        size for both kernels), then for each spread size with the gather's fixed, and keep the fastest.
-        Returns (gather chunk, {chunk: ms per product} of the joint phase); the spread's size is
-        info()["chunk_spread"]."""
+        size for both kernels), then for each spread size with the gather's fixed, then for each persistent-
+        spread residency (blocks per SM 1, 2, 3, or as many as fit = 0), and keep the fastest. Returns
+        (gather chunk, {chunk: ms per product} of the joint phase); the spread's size and residency are
+        info()["chunk_spread"] and info()["spread_blocks_per_sm"], their timings autotune_spread_times and
+        autotune_residency_times."""
         vv, nrhs = self._rhs(v)
         chosen = ctypes.c_int(0)
         nc = len(self.AUTOTUNE_CHUNKS)
-        times = (ctypes.c_double * (2 * nc))()
+        times = (ctypes.c_double * (2 * nc + 4))()
         native.check(self._ready().addker_autotune(self._plan, ctypes.c_void_p(vv.data_ptr()), nrhs,
                                                     ctypes.byref(chosen), times, len(times)), "addker_autotune")
-        self.autotune_spread_times = dict(zip(self.AUTOTUNE_CHUNKS, list(times)[nc:]))
+        self.autotune_spread_times = dict(zip(self.AUTOTUNE_CHUNKS, list(times)[nc:2 * nc]))
+        self.autotune_residency_times = dict(zip((1, 2, 3, 0), list(times)[2 * nc:]))
         return chosen.value, dict(zip(self.AUTOTUNE_CHUNKS, list(times)[:nc]))
 
     STAGES = ("clear", "spread", "transform", "gather", "window_sum")
@@ -302,7 +305,7 @@ class AddKer:
         native.check(native.lib().addker_sync(self._plan), "addker_sync")
 
     def info(self):
-        cap = 9 + 4 * self.P
+        cap = 10 + 4 * self.P
         buf = (ctypes.c_int64 * cap)()
         n = native.lib().addker_info(self._plan, buf, cap)
         vals = list(buf[:n])
@@ -311,7 +314,7 @@ class AddKer:
                 "windows": [dict(d=vals[4 + 4 * s], M=vals[5 + 4 * s], n=vals[6 + 4 * s], cells=vals[7 + 4 * s])
                             for s in range(self.P)],
                 "slots": vals[e], "graphs": vals[e + 1], "graph_replays": vals[e + 2], "chunk": vals[e + 3],
-                "chunk_spread": vals[e + 4]}
+                "chunk_spread": vals[e + 4], "spread_blocks_per_sm": vals[e + 5]}
 
     def debug_stage(self, window, stage, v):
         """Stage 0: spread grid (n^d doubles); stage 1: adjoint NFFT S_k (complex M^d). Synchronous."""

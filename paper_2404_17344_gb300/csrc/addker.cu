@@ -1625,6 +1625,18 @@ int addker_autotune(addker_plan* plan, const float* v, int nrhs, int* chosen, do
         if (times && nc + c < cap) times[nc + c] = ms;
         if (ms < best_ms) { best_ms = ms; best_sp = cand[c]; }
     }
+    // phase 3: the persistent spread's residency, blocks per SM 1, 2, 3 and as many as fit (0)
+    static const int res[] = {1, 2, 3, 0};
+    const int sp_blocks0 = p.sp_blocks;
+    int best_res = sp_blocks0;
+    for (int c = 0; c < 4 && status == ADDKER_OK; ++c) {
+        p.sp_blocks = res[c];
+        const double ms = time_items(best, best_sp);
+        if (status != ADDKER_OK) break;
+        if (times && 2 * nc + c < cap) times[2 * nc + c] = ms;
+        if (ms < best_ms) { best_ms = ms; best_res = res[c]; }
+    }
+    p.sp_blocks = status == ADDKER_OK ? best_res : sp_blocks0;
     cudaStreamSynchronize(p.stream);
     if (status == ADDKER_OK) status = build_items(p, best, best_sp);
     clear_graphs(p);
@@ -1985,6 +1997,7 @@ int addker_info(const addker_plan* plan, int64_t* info, int cap)
     v.push_back(p.graph_replays);
     v.push_back(p.chunk);
     v.push_back(p.chunk_sp);
+    v.push_back(p.sp_blocks);
     for (int i = 0; i < cap && i < (int)v.size(); ++i) info[i] = v[i];
     return (int)v.size();
 }

@@ -876,6 +876,21 @@ static int resident_blocks(K kernel, int threads)
     return nb;
 }
 
+// Blocks of a persistent spread: as many as fit (sp_blocks = 0) or sp_blocks per SM (autotuned), never more
+// than the units need.
+template <typename K>
+static int spread_blocks(const Plan& p, K kernel, int units)
+{
+    int nb = resident_blocks(kernel, kWarps * 32);
+    if (p.sp_blocks > 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        nb = std::min(nb, p.sp_blocks * std::max(sms, 1));
+    }
+    return std::max(1, std::min(nb, (units + kWarps - 1) / kWarps));
+}
+
 // Items of one kind for one window, or for all windows (window < 0).
 static void item_range(const Plan& p, int kind, int window, int* lo, int* hi, bool spread = false)
 {
@@ -903,11 +918,11 @@ cudaError_t launch_spread(const Plan& p, int window, const float* v, int64_t ldv
         if (hi > lo) {
             const int n = hi - lo, units = n * nrhs;
             if (n3 == n) {                    // 3-D items only: the kernel without the per-unit branch
-                const int nb = std::min(resident_blocks(k_spread3_w8, kWarps * 32), (units + kWarps - 1) / kWarps);
+                const int nb = spread_blocks(p, k_spread3_w8, units);
                 launch_k(false, k_spread3_w8, dim3(nb), dim3(kWarps * 32), 0, st, p.items + lo, n, units, p.counters,
                          wd, v, ldv, p.poly);
             } else {
-                const int nb = std::min(resident_blocks(k_spread_w8_all, kWarps * 32), (units + kWarps - 1) / kWarps);
+                const int nb = spread_blocks(p, k_spread_w8_all, units);
                 launch_k(false, k_spread_w8_all, dim3(nb), dim3(kWarps * 32), 0, st, p.items + lo, n, units, n3,
                          p.counters, wd, v, ldv, p.poly);
             }
@@ -928,7 +943,7 @@ cudaError_t launch_spread(const Plan& p, int window, const float* v, int64_t ldv
             case kKindFast3: {
                 // persistent: as many blocks as fit at once, units taken from a zeroed counter
                 const int units = n * nrhs;
-                const int nb = std::min(resident_blocks(k_spread3_w8, kWarps * 32), (units + kWarps - 1) / kWarps);
+                const int nb = spread_blocks(p, k_spread3_w8, units);
                 launch_k(pdl, k_spread3_w8, dim3(nb), T, 0, st, it, n, units, p.counters, wd, v, ldv, p.poly);
                 break;
             }

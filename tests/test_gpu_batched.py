@@ -197,6 +197,8 @@ def test_autotune_keeps_results(torch_cuda, cfg, N, nrhs):
     assert chosen in op.AUTOTUNE_CHUNKS and info["chunk"] == chosen
     assert info["chunk_spread"] in op.AUTOTUNE_CHUNKS
     assert all(t > 0 for t in times.values()) and all(t > 0 for t in op.autotune_spread_times.values())
+    assert all(t > 0 for t in op.autotune_residency_times.values())
+    assert info["spread_blocks_per_sm"] in (0, 1, 2, 3)
     # the spread phase's entry for the joint winner repeats the joint timing
     assert op.autotune_spread_times[chosen] == times[chosen]
     for _ in range(3):
