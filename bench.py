@@ -6,7 +6,8 @@ cutoff m = 4 (N(0,1) features scaled into the ball of radius 1/4 - eps_B/2; synt
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--N 1000000]
   python bench.py --mode batched [--nrhs 64]        (secondary: 7 mixed windows, 64 right-hand sides)
-  python bench.py --mode gp [--nrhs 17 --beta 1 --tol 1e-6 --maxit 100]   (secondary: GP gradient, N = 2e6)
+  python bench.py --mode gp [--nrhs 17 --beta 0.01 --tol 1e-6 --maxit 100]   (secondary: GP gradient, N = 2e6)
+  python bench.py --mode grad                       (secondary: vector-Jacobian product, N = 2e5)
 
 --gpus N > 1 runs under torchrun, one rank per GPU: independent replicas (the product needs no
 exchange between GPUs at this size), weak scaling; value = all ranks' units / max-over-ranks time.
@@ -455,6 +456,8 @@ def run_batched(args, rank, world, local_rank):
                       "N": N, "nrhs": R, "chunk": chunk, "chunk_spread": op.info()["chunk_spread"],
                       "autotune_ms": tune_ms, "autotune_spread_ms": op.autotune_spread_times,
                       "spread_blocks_per_sm": op.info()["spread_blocks_per_sm"],
+                      "spread_tile": op.info()["spread_tile"],
+                      "autotune_tile_ms": {str(k): v for k, v in op.autotune_tile_times.items()},
                       "autotune_residency_ms": {str(k): v for k, v in op.autotune_residency_times.items()}},
            "per_rhs_ms": ms / R, "single_rhs_ms": single_ms, "speedup_per_solve_vs_single": single_ms / (ms / R),
            "clocks": clk.summary(), "accuracy": acc, "plan": {k: v for k, v in op.info().items() if k != "windows"}}
@@ -516,6 +519,62 @@ def run_gp(args, rank, world, local_rank):
     op.close()
 
 
+def run_grad(args, rank, world, local_rank):
+    """Secondary workload (differentiation): the mixture-of-Gaussians configuration (N = 2e5, d = 12, four
+    windows of 3, ell = 0.3, 0.5, 0.7, 1.0, M = 32, m = 4); one step = one vector-Jacobian product of
+    f = w^T K v (addker_vjp): the gradients with respect to v, every ell_s, sigma_f and the N x 12 point
+    coordinates. Accuracy: the parameter gradients against the oracle's FP64 NFFT gradients."""
+    import numpy as np
+    torch, dev, gpu_id = _setup_secondary(args, local_rank)
+    import workloads
+    from paper_2404_17344_gb300 import AddKer
+    N = args.N if args.N != 1_000_000 else 200_000
+    wl = workloads.make("c2", N=N)
+    op = AddKer(torch.from_numpy(wl.points).to(dev), wl.windows, wl.ell, wl.sigma_f, wl.bandwidth, wl.cutoff)
+    v_np, w_np = wl.vector(), wl.vector(which=2)
+    v, w = torch.from_numpy(v_np).to(dev), torch.from_numpy(w_np).to(dev)
+    for _ in range(args.warmup):
+        op.vjp(v, w)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(gpu_id) as clk:
+        for a, b in ev:
+            a.record()
+            gv, gt, gx = op.vjp(v, w)
+            b.record()
+        torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    # one fused product for comparison (K v and every dK/d ell_s v)
+    for _ in range(3):
+        op.matvec_all(v)
+    torch.cuda.synchronize()
+    a1, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a1.record()
+    for _ in range(10):
+        op.matvec_all(v)
+    b1.record()
+    torch.cuda.synchronize()
+    fused_ms = a1.elapsed_time(b1) / 10
+    import oracle
+    rv, rell, rsf, rx = oracle.gradients.nfft_grad(wl.points, wl.windows, wl.ell, wl.sigma_f, v_np, w_np,
+                                                   wl.bandwidth, wl.cutoff)
+    gt = gt.cpu().numpy()
+    r = lambda a, b: float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+    out = {"metric": "vector-Jacobian products of w^T K v per sec (grad v, ell, sigma_f, points), N=200k, 4 windows of 3",
+           "value": 1e3 / ms, "unit": "gradients/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": f"c2-shaped at N={N}: d=12, mixture of 4 Gaussians, 4 windows of 3, "
+                                  "ell=(0.3,0.5,0.7,1.0), M=32, m=4", "N": N},
+           "fused_product_ms": fused_ms, "vjp_over_product": ms / fused_ms,
+           "accuracy": {"grad_v_vs_fp64_nfft": r(gv.cpu().numpy(), rv), "grad_ell_vs_fp64_nfft": r(gt[:wl.P], rell),
+                        "grad_sigma_f_vs_fp64_nfft": abs(gt[wl.P] - rsf) / abs(rsf),
+                        "grad_points_vs_fp64_nfft": r(gx.cpu().numpy(), rx)},
+           "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+    op.close()
+
+
 def run_cpu_times(args, rank):
     """CPU context for the headline workload (no GPU): one full-N FP64 oracle product on the host
     cores (the oracle's OpenMP threads; OMP_NUM_THREADS=1 gives the one-core figure) and, with
@@ -552,9 +611,10 @@ def main():
     ap.add_argument("--cpu-reps", type=int, default=3, help="oracle products timed for cpu_baseline")
     ap.add_argument("--check-rows", type=int, default=4096)
     ap.add_argument("--no-check", action="store_true")
-    ap.add_argument("--mode", default="product", choices=["product", "batched", "gp", "cpu"],
+    ap.add_argument("--mode", default="product", choices=["product", "batched", "gp", "grad", "cpu"],
                     help="product: the headline fused product; batched: 7 mixed windows x 64 right-hand sides; "
-                         "gp: one GP gradient (CG + Hutchinson) per step; cpu: FP64 oracle timings on the host "
+                         "gp: one GP gradient (CG + Hutchinson) per step; grad: one vector-Jacobian product per "
+                         "step (differentiation configuration); cpu: FP64 oracle timings on the host "
                          "cores (no GPU)")
     ap.add_argument("--nrhs", type=int, default=64, help="right-hand sides per step (batched), 1 + probes (gp)")
     ap.add_argument("--beta", type=float, default=0.01,
@@ -574,6 +634,8 @@ def main():
         run_batched(args, rank, world, local_rank)
     elif args.mode == "cpu":
         run_cpu_times(args, rank)
+    elif args.mode == "grad":
+        run_grad(args, rank, world, local_rank)
     elif args.mode == "gp":
         if args.nrhs == 64:
             args.nrhs = 17                       # y and 16 probes

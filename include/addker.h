@@ -23,7 +23,8 @@
  *
  * Entry points:
  *   plan         addker_opts_default, addker_setup, addker_set_params, addker_set_stream,
- *                addker_set_graphs, addker_set_precond, addker_autotune, addker_free, addker_info
+ *                addker_set_graphs, addker_set_precond, addker_set_schedule, addker_autotune, addker_free,
+ *                addker_info
  *   products     addker_matvec, addker_dmatvec, addker_matvec_all (device buffers),
  *                addker_matvec_all_host (host buffers), addker_fastsum_noalloc (no plan)
  *   gradients    addker_vjp (w^T K v with respect to v, ell, sigma_f and the points)
@@ -194,14 +195,26 @@ int addker_set_graphs(addker_plan* plan, int enable);
  * three timed products per candidate, without graphs: first one item size for both kernels, chunk in
  * {64, 128, 256, 512, 1024}; then, with the gather's size fixed at the fastest, the spread's size over the
  * same candidates; then the persistent spread's residency, 1, 2 or 3 blocks per SM or as many as fit
- * (fewer resident warps contend less for the grid's atomic adds, more hide more latency). The fastest
- * setting is kept for later products; chosen (host, may be NULL) receives the gather's size (the spread's
- * and the residency are addker_info's last two values) and times (host, may be NULL) up to `cap`
- * milliseconds per product: the five joint candidates, the five spread candidates, then the four
- * residencies. Allocates and frees its own output buffers; synchronous on the plan's stream. The paper has
+ * (fewer resident warps contend less for the grid's atomic adds, more hide more latency); then the 3-D
+ * spread's register tile (each lane accumulating a 4 x 4 x 2 or an 8 x 2 x 2 block of the 8 x 8 x 8 box:
+ * the second needs half the packed products per point and one more shared load). The fastest setting is
+ * kept for later products; chosen (host, may be NULL) receives the gather's size (the spread's size,
+ * residency and tile are addker_info's last three values) and times (host, may be NULL) up to `cap`
+ * milliseconds per product: the five joint candidates, the five spread candidates, the four residencies,
+ * then the two tiles. Allocates and frees its own output buffers; synchronous on the plan's stream. The paper has
  * no counterpart (its library runs on the CPU): these are scheduling choices of the GPU path.
  */
 int addker_autotune(addker_plan* plan, const float* v, int nrhs, int* chosen, double* times, int cap);
+
+/*
+ * Set the schedule that addker_autotune chooses, directly (for instance one tuned earlier): work items
+ * of at most `chunk` points for the gathers and `chunk_spread` for the spread (16 .. 4096; the items are
+ * re-cut when a size changes), the persistent spread's blocks per SM (0 = as many as fit, else 1 .. 8) and
+ * the 3-D spread's register tile (0 or 1, see addker_autotune). Results do not depend on the schedule
+ * beyond FP32 rounding order. EINVAL for values outside these ranges, ENOMEM if re-cutting fails.
+ * Synchronises the plan's stream and drops captured graphs.
+ */
+int addker_set_schedule(addker_plan* plan, int chunk, int chunk_spread, int spread_blocks, int spread_tile);
 
 /*
  * Conjugate gradients for the regression system (K + beta I) x = y (Sec. 3.3, eq. "regression_system";
@@ -381,7 +394,8 @@ int addker_prescale_cube(const float* X, int64_t N, int d, const int* win_off, c
  *   then [4+4P] right-hand-side slots allocated  [5+4P] captured product graphs held
  *   [6+4P] product graph replays so far  [7+4P] points per gather work item at most
  *   [8+4P] points per spread work item at most (x8 for 2-D windows)
- *   [9+4P] blocks per SM of the persistent spread (0: as many as fit).
+ *   [9+4P] blocks per SM of the persistent spread (0: as many as fit)
+ *   [10+4P] register tile of the 3-D spread (0: a 4 x 4 x 2 block of the 8 x 8 x 8 box per lane, 1: 8 x 2 x 2).
  * Returns the number of values available.
  */
 int addker_info(const addker_plan* plan, int64_t* info, int cap);

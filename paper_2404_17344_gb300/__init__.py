@@ -206,6 +206,12 @@ class AddKer:
         """Replay repeated identical products as CUDA graphs (default on); False launches every kernel."""
         native.check(self._ready().addker_set_graphs(self._plan, 1 if enable else 0), "addker_set_graphs")
 
+    def set_schedule(self, chunk=256, chunk_spread=256, spread_blocks=0, spread_tile=0):
+        """Work-item sizes, persistent-spread blocks per SM (0 = as many as fit) and 3-D spread register tile
+        (addker_set_schedule): the choices addker_autotune makes, set directly."""
+        native.check(self._ready().addker_set_schedule(self._plan, int(chunk), int(chunk_spread), int(spread_blocks),
+                                                        int(spread_tile)), "addker_set_schedule")
+
     def set_precond(self, band):
         """CG preconditioner with every window's Fourier modes |k|_inf <= band (addker_set_precond; 0 = plain CG,
         default 1)."""
@@ -272,18 +278,20 @@ class AddKer:
     def autotune(self, v):
         """Time the fused product on v ((N,) or (N, nrhs)) for each work-item size in AUTOTUNE_CHUNKS (one
         size for both kernels), then for each spread size with the gather's fixed, then for each persistent-
-        spread residency (blocks per SM 1, 2, 3, or as many as fit = 0), and keep the fastest. Returns
+        spread residency (blocks per SM 1, 2, 3, or as many as fit = 0), then for each 3-D spread register
+        tile (0, 1), and keep the fastest. Returns
         (gather chunk, {chunk: ms per product} of the joint phase); the spread's size and residency are
-        info()["chunk_spread"] and info()["spread_blocks_per_sm"], their timings autotune_spread_times and
-        autotune_residency_times."""
+        info()["chunk_spread"], info()["spread_blocks_per_sm"] and info()["spread_tile"], their timings
+        autotune_spread_times, autotune_residency_times and autotune_tile_times."""
         vv, nrhs = self._rhs(v)
         chosen = ctypes.c_int(0)
         nc = len(self.AUTOTUNE_CHUNKS)
-        times = (ctypes.c_double * (2 * nc + 4))()
+        times = (ctypes.c_double * (2 * nc + 6))()
         native.check(self._ready().addker_autotune(self._plan, ctypes.c_void_p(vv.data_ptr()), nrhs,
                                                     ctypes.byref(chosen), times, len(times)), "addker_autotune")
         self.autotune_spread_times = dict(zip(self.AUTOTUNE_CHUNKS, list(times)[nc:2 * nc]))
-        self.autotune_residency_times = dict(zip((1, 2, 3, 0), list(times)[2 * nc:]))
+        self.autotune_residency_times = dict(zip((1, 2, 3, 0), list(times)[2 * nc:2 * nc + 4]))
+        self.autotune_tile_times = dict(zip((0, 1), list(times)[2 * nc + 4:]))
         return chosen.value, dict(zip(self.AUTOTUNE_CHUNKS, list(times)[:nc]))
 
     STAGES = ("clear", "spread", "transform", "gather", "window_sum")
@@ -305,7 +313,7 @@ class AddKer:
         native.check(native.lib().addker_sync(self._plan), "addker_sync")
 
     def info(self):
-        cap = 10 + 4 * self.P
+        cap = 11 + 4 * self.P
         buf = (ctypes.c_int64 * cap)()
         n = native.lib().addker_info(self._plan, buf, cap)
         vals = list(buf[:n])
@@ -314,7 +322,7 @@ class AddKer:
                 "windows": [dict(d=vals[4 + 4 * s], M=vals[5 + 4 * s], n=vals[6 + 4 * s], cells=vals[7 + 4 * s])
                             for s in range(self.P)],
                 "slots": vals[e], "graphs": vals[e + 1], "graph_replays": vals[e + 2], "chunk": vals[e + 3],
-                "chunk_spread": vals[e + 4], "spread_blocks_per_sm": vals[e + 5]}
+                "chunk_spread": vals[e + 4], "spread_blocks_per_sm": vals[e + 5], "spread_tile": vals[e + 6]}
 
     def debug_stage(self, window, stage, v):
         """Stage 0: spread grid (n^d doubles); stage 1: adjoint NFFT S_k (complex M^d). Synchronous."""

@@ -1554,6 +1554,20 @@ int addker_set_params(addker_plan* plan, const double* ell, double sigma_f)
     return upload_scales(p);
 }
 
+int addker_set_schedule(addker_plan* plan, int chunk, int chunk_spread, int spread_blocks, int spread_tile)
+{
+    if (!plan || chunk < 16 || chunk > 4096 || chunk_spread < 16 || chunk_spread > 4096 || spread_blocks < 0 ||
+        spread_blocks > 8 || (spread_tile != 0 && spread_tile != 1))
+        return ADDKER_EINVAL;
+    Plan& p = plan->p;
+    CK(cudaStreamSynchronize(p.stream));
+    clear_graphs(p);
+    if (chunk != p.chunk || chunk_spread != p.chunk_sp) CS(build_items(p, chunk, chunk_spread));
+    p.sp_blocks = spread_blocks;
+    p.sp_tile = spread_tile;
+    return ADDKER_OK;
+}
+
 int addker_set_precond(addker_plan* plan, int band)
 {
     if (!plan || band < 0 || band > kPcMaxBand) return ADDKER_EINVAL;
@@ -1637,6 +1651,17 @@ int addker_autotune(addker_plan* plan, const float* v, int nrhs, int* chosen, do
         if (ms < best_ms) { best_ms = ms; best_res = res[c]; }
     }
     p.sp_blocks = status == ADDKER_OK ? best_res : sp_blocks0;
+    // phase 4: the 3-D spread's register tile (4 a x 4 b x 2 c or 8 a x 2 b x 2 c per lane)
+    const int sp_tile0 = p.sp_tile;
+    int best_tile = sp_tile0;
+    for (int c = 0; c < 2 && status == ADDKER_OK; ++c) {
+        p.sp_tile = c;
+        const double ms = time_items(best, best_sp);
+        if (status != ADDKER_OK) break;
+        if (times && 2 * nc + 4 + c < cap) times[2 * nc + 4 + c] = ms;
+        if (ms < best_ms) { best_ms = ms; best_tile = c; }
+    }
+    p.sp_tile = status == ADDKER_OK ? best_tile : sp_tile0;
     cudaStreamSynchronize(p.stream);
     if (status == ADDKER_OK) status = build_items(p, best, best_sp);
     clear_graphs(p);
@@ -1998,6 +2023,7 @@ int addker_info(const addker_plan* plan, int64_t* info, int cap)
     v.push_back(p.chunk);
     v.push_back(p.chunk_sp);
     v.push_back(p.sp_blocks);
+    v.push_back(p.sp_tile);
     for (int i = 0; i < cap && i < (int)v.size(); ++i) info[i] = v[i];
     return (int)v.size();
 }

@@ -106,6 +106,7 @@ struct Plan {
     int chunk = kItemPoints;              // points per work item at most (gathers)
     int chunk_sp = kItemPoints;           // points per spread work item at most (x8 for 2-D windows)
     int sp_blocks = 0;                    // blocks per SM of the persistent spreads (0: as many as fit)
+    int sp_tile = 0;                      // register tile of the 3-D spread (0: 4x4x2 per lane, 1: 8x2x2)
     std::vector<std::vector<int4>> cells; // per window: non-empty cells (first point, count, packed cell, s)
     std::vector<int> item_begin[kKinds];
     std::vector<int> item_begin_sp[kKinds]; // the spread's list (larger items for 2-D windows), same array

@@ -69,6 +69,88 @@ __device__ __forceinline__ void mom_unit_end(MomAcc& acc, float* mm, const WinDe
     acc.a += (double)t;
 }
 
+// The 3-D spread's register tile (m = 4, W = 8): each lane of half-warp hw holds 32 values of the item's
+// 8x8x8 box, acc[16] float2, summed over the staged points its half takes (alternate points). Two shapes:
+//   TILE 0: a in 4ah..4ah+3, b in 4bh..4bh+3, c in {2cq, 2cq+1}: acc[(2a' + p) 2 + i] =
+//           (g[4ah+a'][4bh+2p][2cq+i], g[4ah+a'][4bh+2p+1][2cq+i]); per point 3 shared loads (40 B),
+//           4 packed products y (x) z and 16 packed FMAs;
+//   TILE 1: a in 0..7, b in {2bp, 2bp+1}, c in {2cq, 2cq+1}: acc[2a + i] = (g[a][2bp][2cq+i], g[a][2bp+1][2cq+i]);
+//           per point 4 shared loads (48 B), 2 packed products and 16 packed FMAs.
+// The duplicated operands the packed FMAs need are formed in registers. Staged rows: x v [8] | y [8] | z [8].
+template <int TILE>
+__device__ __forceinline__ void spread3_points(float2 (&acc)[16], const float* ws, int stride, int cnt, int lane)
+{
+    const int hw = lane >> 4, cq = lane & 3;
+    const float* src = ws + hw * stride;
+    if (TILE == 0) {
+        const int ah = (lane >> 3) & 1, bh = (lane >> 2) & 1;
+#pragma unroll 2
+        for (int j = 0; j < cnt; j += 2, src += 2 * stride) {
+            const float4 xa = *reinterpret_cast<const float4*>(src + 4 * ah);         // a = 4ah .. 4ah+3
+            const float4 yb = *reinterpret_cast<const float4*>(src + 8 + 4 * bh);     // b = 4bh .. 4bh+3
+            const float2 zc = *reinterpret_cast<const float2*>(src + 16 + 2 * cq);    // c = 2cq, 2cq+1
+            const float2 Y[2] = {f2(yb.x, yb.y), f2(yb.z, yb.w)};
+            const float2 Z[2] = {f2(zc.x, zc.x), f2(zc.y, zc.y)};
+            const float2 X[4] = {f2(xa.x, xa.x), f2(xa.y, xa.y), f2(xa.z, xa.z), f2(xa.w, xa.w)};
+            float2 B[2][2];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) B[q >> 1][q & 1] = __fmul2_rn(Y[q >> 1], Z[q & 1]);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[a * 4 + q] = __ffma2_rn(X[a], B[q >> 1][q & 1], acc[a * 4 + q]);
+        }
+    } else {
+        const int bp = (lane >> 2) & 3;
+#pragma unroll 2
+        for (int j = 0; j < cnt; j += 2, src += 2 * stride) {
+            const float4 x0 = *reinterpret_cast<const float4*>(src);                  // a = 0 .. 3
+            const float4 x1 = *reinterpret_cast<const float4*>(src + 4);              // a = 4 .. 7
+            const float2 yb = *reinterpret_cast<const float2*>(src + 8 + 2 * bp);     // b = 2bp, 2bp+1
+            const float2 zc = *reinterpret_cast<const float2*>(src + 16 + 2 * cq);    // c = 2cq, 2cq+1
+            const float2 B[2] = {__fmul2_rn(yb, f2(zc.x, zc.x)), __fmul2_rn(yb, f2(zc.y, zc.y))};
+            const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+                const float2 X = f2(xs[a], xs[a]);
+                acc[2 * a] = __ffma2_rn(X, B[0], acc[2 * a]);
+                acc[2 * a + 1] = __ffma2_rn(X, B[1], acc[2 * a + 1]);
+            }
+        }
+    }
+}
+
+// Sum the two halves' tiles (half hw keeps the values with c = 2cq + hw and receives its partner's) and add
+// the 16 kept values per lane to the grid of window P, right-hand side r, for the item's cell.
+template <int TILE>
+__device__ __forceinline__ void spread3_flush(float2 (&acc)[16], const WinDev* P, const int4 it, int r, int lane)
+{
+    const int hw = lane >> 4, cq = lane & 3;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float2 send = hw ? acc[2 * k] : acc[2 * k + 1];
+        float2 keep = hw ? acc[2 * k + 1] : acc[2 * k];
+        keep.x += __shfl_xor_sync(0xffffffffu, send.x, 16);
+        keep.y += __shfl_xor_sync(0xffffffffu, send.y, 16);
+        acc[2 * k] = keep;
+    }
+    const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff, cz = (it.z >> 16) & 0xff;
+    const int ox = cx - 3 - P->lo[0], oy = cy - 3 - P->lo[1], oz = cz - 3 - P->lo[2];
+    const int sy = P->box[2], sx = P->box[1] * P->box[2];
+    const int a0 = TILE == 0 ? 4 * ((lane >> 3) & 1) : 0;
+    const int b0 = TILE == 0 ? 4 * ((lane >> 2) & 1) : 2 * ((lane >> 2) & 3);
+    const size_t o0 = r * P->gsz + (size_t)(ox + a0) * sx + (size_t)(oy + b0) * sy + oz + 2 * cq + hw;
+    float* g = P->grid + o0;
+    double* ge = P->grid64 ? P->grid64 + o0 : nullptr;
+    // k-th kept pair: TILE 0 (a = k / 2, b = 2 (k % 2) + {0, 1}); TILE 1 (a = k, b = {0, 1})
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const size_t o = TILE == 0 ? (size_t)(k >> 1) * sx + (size_t)(2 * (k & 1)) * sy : (size_t)k * sx;
+        grid_add(g + o, ge ? ge + o : nullptr, acc[2 * k].x);
+        grid_add(g + o + sy, ge ? ge + o + sy : nullptr, acc[2 * k].y);
+    }
+}
+
 // fast 3-D spread, m = 4 (W = 8)
 // Staged per point (STRIDE floats): x_a v [8] | y [8] | z [8]. The two half-warps take alternate
 // staged points (hw = lane >> 4). Within a half-warp, lane (ah, bh, cq) accumulates
@@ -82,6 +164,7 @@ __device__ __forceinline__ void mom_unit_end(MomAcc& acc, float* mm, const WinDe
 // ahead, and loads the first batch of the next unit while it finishes the current one, so neither
 // the chain item -> points -> v at the start of an item nor the drain of the atomic adds at its end
 // stalls the warp. Unit u is item u % nitems of right-hand side u / nitems.
+template <int TILE>
 __global__ void __launch_bounds__(kWarps * 32, 4) k_spread3_w8(const int4* __restrict__ items, int nitems,
                                                               int nunits, int* __restrict__ counter,
                                                               const WinDev* __restrict__ wins,
@@ -93,7 +176,6 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_spread3_w8(const int4* __res
     __shared__ __align__(16) float sw[kWarps][32 * STRIDE];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* ws = sw[warp];
-    const int hw = lane >> 4, ah = (lane >> 3) & 1, bh = (lane >> 2) & 1, cq = lane & 3;
 
     int u = 0;
     if (lane == 0) u = atomicAdd(counter, 1);
@@ -118,11 +200,9 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_spread3_w8(const int4* __res
     float mm[5] = {0.f, 0.f, 0.f, 0.f, 0.f};      // moments of the quadratic split over this unit
     MomAcc macc = {0.0, -1};
     while (true) {
-        float2 acc[4][2][2];
+        float2 acc[16];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[a][q >> 1][q & 1] = f2(0.f, 0.f);
+        for (int q = 0; q < 16; ++q) acc[q] = f2(0.f, 0.f);
         const int count = it.y;
         const int n = P->n;
         const bool more = un < nunits;
@@ -160,52 +240,10 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_spread3_w8(const int4* __res
             __syncwarp();
             // rows cnt .. 31 hold zeros (lanes without a point stage zero weights), so an odd count is safe
             const int cnt = min(32, count - base);
-            const float* src = ws + hw * STRIDE;
-#pragma unroll 2
-            for (int j = 0; j < cnt; j += 2, src += 2 * STRIDE) {
-                const float4 xa = *reinterpret_cast<const float4*>(src + 4 * ah);         // a = 4ah .. 4ah+3
-                const float4 yb = *reinterpret_cast<const float4*>(src + 8 + 4 * bh);     // b = 4bh .. 4bh+3
-                const float2 zc = *reinterpret_cast<const float2*>(src + 16 + 2 * cq);    // c = 2cq, 2cq+1
-                const float2 Y[2] = {f2(yb.x, yb.y), f2(yb.z, yb.w)};
-                const float2 Z[2] = {f2(zc.x, zc.x), f2(zc.y, zc.y)};
-                const float2 X[4] = {f2(xa.x, xa.x), f2(xa.y, xa.y), f2(xa.z, xa.z), f2(xa.w, xa.w)};
-                float2 B[2][2];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) B[q >> 1][q & 1] = __fmul2_rn(Y[q >> 1], Z[q & 1]);
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        acc[a][q >> 1][q & 1] = __ffma2_rn(X[a], B[q >> 1][q & 1], acc[a][q >> 1][q & 1]);
-            }
+            spread3_points<TILE>(acc, ws, STRIDE, cnt, lane);
             __syncwarp();
         }
-        // sum the halves: half hw keeps the values with i = hw and receives its partner's
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                const float2 send = hw ? acc[a][p][0] : acc[a][p][1];
-                float2 keep = hw ? acc[a][p][1] : acc[a][p][0];
-                keep.x += __shfl_xor_sync(0xffffffffu, send.x, 16);
-                keep.y += __shfl_xor_sync(0xffffffffu, send.y, 16);
-                acc[a][p][0] = keep;
-            }
-        // flush: grid index of (a, b, c) relative to the box origin, c = 2cq + hw
-        const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff, cz = (it.z >> 16) & 0xff;
-        const int ox = cx - 3 - P->lo[0], oy = cy - 3 - P->lo[1], oz = cz - 3 - P->lo[2];
-        const int sy = P->box[2], sx = P->box[1] * P->box[2];
-        const size_t o0 = r * P->gsz + (size_t)(ox + 4 * ah) * sx + (size_t)(oy + 4 * bh) * sy + oz + 2 * cq + hw;
-        float* g = P->grid + o0;
-        double* ge = P->grid64 ? P->grid64 + o0 : nullptr;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const size_t oa = (size_t)a * sx;
-            grid_add(g + oa, ge ? ge + oa : nullptr, acc[a][0][0].x);
-            grid_add(g + oa + sy, ge ? ge + oa + sy : nullptr, acc[a][0][0].y);
-            grid_add(g + oa + 2 * sy, ge ? ge + oa + 2 * sy : nullptr, acc[a][1][0].x);
-            grid_add(g + oa + 3 * sy, ge ? ge + oa + 3 * sy : nullptr, acc[a][1][0].y);
-        }
+        spread3_flush<TILE>(acc, P, it, r, lane);
         if (split) mom_unit_end(macc, mm, wins, it.w, r, lane);
         if (!more) break;
         // advance: the prefetched unit becomes current; take the one after it
@@ -494,6 +532,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_spread_lowd_w8(const int4* __re
 // 3-D unit's first batch is prefetched by the unit before it only when that one is 3-D as well.
 // Unit u takes item (u % nitems + rot) % nitems: with rot = the number of 3-D items the low-d items
 // (latency-bound, few) go first and overlap the 3-D work, whose light items then form the tail.
+template <int TILE>
 __global__ void __launch_bounds__(kWarps * 32, 4) k_spread_w8_all(const int4* __restrict__ items, int nitems,
                                                               int nunits, int rot, int* __restrict__ counter,
                                                               const WinDev* __restrict__ wins,
@@ -505,7 +544,6 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_spread_w8_all(const int4* __
     __shared__ __align__(16) float sw[kWarps][32 * STRIDE];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* ws = sw[warp];
-    const int hw = lane >> 4, ah = (lane >> 3) & 1, bh = (lane >> 2) & 1, cq = lane & 3;
 
     int u = 0;
     if (lane == 0) u = atomicAdd(counter, 1);
@@ -548,11 +586,9 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_spread_w8_all(const int4* __
             pn = pts[lane];
             vn = __ldg(vr + __float_as_int(pn.w));
         }
-        float2 acc[4][2][2];
+        float2 acc[16];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[a][q >> 1][q & 1] = f2(0.f, 0.f);
+        for (int q = 0; q < 16; ++q) acc[q] = f2(0.f, 0.f);
         const int count = it.y;
         const int n = P->n;
         const bool split = P->pq != 0.f;
@@ -591,52 +627,10 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_spread_w8_all(const int4* __
             __syncwarp();
             // rows cnt .. 31 hold zeros (lanes without a point stage zero weights), so an odd count is safe
             const int cnt = min(32, count - base);
-            const float* src = ws + hw * STRIDE;
-#pragma unroll 2
-            for (int j = 0; j < cnt; j += 2, src += 2 * STRIDE) {
-                const float4 xa = *reinterpret_cast<const float4*>(src + 4 * ah);         // a = 4ah .. 4ah+3
-                const float4 yb = *reinterpret_cast<const float4*>(src + 8 + 4 * bh);     // b = 4bh .. 4bh+3
-                const float2 zc = *reinterpret_cast<const float2*>(src + 16 + 2 * cq);    // c = 2cq, 2cq+1
-                const float2 Y[2] = {f2(yb.x, yb.y), f2(yb.z, yb.w)};
-                const float2 Z[2] = {f2(zc.x, zc.x), f2(zc.y, zc.y)};
-                const float2 X[4] = {f2(xa.x, xa.x), f2(xa.y, xa.y), f2(xa.z, xa.z), f2(xa.w, xa.w)};
-                float2 B[2][2];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) B[q >> 1][q & 1] = __fmul2_rn(Y[q >> 1], Z[q & 1]);
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        acc[a][q >> 1][q & 1] = __ffma2_rn(X[a], B[q >> 1][q & 1], acc[a][q >> 1][q & 1]);
-            }
+            spread3_points<TILE>(acc, ws, STRIDE, cnt, lane);
             __syncwarp();
         }
-        // sum the halves: half hw keeps the values with i = hw and receives its partner's
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                const float2 send = hw ? acc[a][p][0] : acc[a][p][1];
-                float2 keep = hw ? acc[a][p][1] : acc[a][p][0];
-                keep.x += __shfl_xor_sync(0xffffffffu, send.x, 16);
-                keep.y += __shfl_xor_sync(0xffffffffu, send.y, 16);
-                acc[a][p][0] = keep;
-            }
-        // flush: grid index of (a, b, c) relative to the box origin, c = 2cq + hw
-        const int cx = it.z & 0xff, cy = (it.z >> 8) & 0xff, cz = (it.z >> 16) & 0xff;
-        const int ox = cx - 3 - P->lo[0], oy = cy - 3 - P->lo[1], oz = cz - 3 - P->lo[2];
-        const int sy = P->box[2], sx = P->box[1] * P->box[2];
-        const size_t o0 = r * P->gsz + (size_t)(ox + 4 * ah) * sx + (size_t)(oy + 4 * bh) * sy + oz + 2 * cq + hw;
-        float* g = P->grid + o0;
-        double* ge = P->grid64 ? P->grid64 + o0 : nullptr;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const size_t oa = (size_t)a * sx;
-            grid_add(g + oa, ge ? ge + oa : nullptr, acc[a][0][0].x);
-            grid_add(g + oa + sy, ge ? ge + oa + sy : nullptr, acc[a][0][0].y);
-            grid_add(g + oa + 2 * sy, ge ? ge + oa + 2 * sy : nullptr, acc[a][1][0].x);
-            grid_add(g + oa + 3 * sy, ge ? ge + oa + 3 * sy : nullptr, acc[a][1][0].y);
-        }
+        spread3_flush<TILE>(acc, P, it, r, lane);
         if (split) mom_unit_end(macc, mm, wins, it.w, r, lane);
         primed = n3;
         if (!more) break;
@@ -918,13 +912,15 @@ cudaError_t launch_spread(const Plan& p, int window, const float* v, int64_t ldv
         if (hi > lo) {
             const int n = hi - lo, units = n * nrhs;
             if (n3 == n) {                    // 3-D items only: the kernel without the per-unit branch
-                const int nb = spread_blocks(p, k_spread3_w8, units);
-                launch_k(false, k_spread3_w8, dim3(nb), dim3(kWarps * 32), 0, st, p.items + lo, n, units, p.counters,
-                         wd, v, ldv, p.poly);
+                auto kern = p.sp_tile == 1 ? k_spread3_w8<1> : k_spread3_w8<0>;
+                const int nb = spread_blocks(p, kern, units);
+                launch_k(false, kern, dim3(nb), dim3(kWarps * 32), 0, st, p.items + lo, n, units, p.counters, wd, v,
+                         ldv, p.poly);
             } else {
-                const int nb = spread_blocks(p, k_spread_w8_all, units);
-                launch_k(false, k_spread_w8_all, dim3(nb), dim3(kWarps * 32), 0, st, p.items + lo, n, units, n3,
-                         p.counters, wd, v, ldv, p.poly);
+                auto kern = p.sp_tile == 1 ? k_spread_w8_all<1> : k_spread_w8_all<0>;
+                const int nb = spread_blocks(p, kern, units);
+                launch_k(false, kern, dim3(nb), dim3(kWarps * 32), 0, st, p.items + lo, n, units, n3, p.counters, wd,
+                         v, ldv, p.poly);
             }
             ++launched;
         }
@@ -943,8 +939,9 @@ cudaError_t launch_spread(const Plan& p, int window, const float* v, int64_t ldv
             case kKindFast3: {
                 // persistent: as many blocks as fit at once, units taken from a zeroed counter
                 const int units = n * nrhs;
-                const int nb = spread_blocks(p, k_spread3_w8, units);
-                launch_k(pdl, k_spread3_w8, dim3(nb), T, 0, st, it, n, units, p.counters, wd, v, ldv, p.poly);
+                auto kern = p.sp_tile == 1 ? k_spread3_w8<1> : k_spread3_w8<0>;
+                const int nb = spread_blocks(p, kern, units);
+                launch_k(pdl, kern, dim3(nb), T, 0, st, it, n, units, p.counters, wd, v, ldv, p.poly);
                 break;
             }
             case kKindLow1: launch_k(pdl, k_spread_lowd_w8<1>, warps, T, 0, st, it, n, wd, v, ldv, p.poly); break;

@@ -49,6 +49,7 @@ SIGNATURES = {
     "addker_set_stream": (_I, [_VP, _VP]),
     "addker_set_graphs": (_I, [_VP, _I]),
     "addker_set_precond": (_I, [_VP, _I]),
+    "addker_set_schedule": (_I, [_VP, _I, _I, _I, _I]),
     "addker_autotune": (_I, [_VP, _VP, _I, _VP, _VP, _I]),
     "addker_gsi": (_I, [_VP, _VP, _I, _VP, _VP, _VP]),
     "addker_cg": (_I, [_VP, ctypes.c_double, _VP, _VP, _I, ctypes.c_double, _I, _VP, _VP]),

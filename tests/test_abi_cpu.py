@@ -108,6 +108,7 @@ def test_product_calls_reject_null_plan(lib):
     assert lib.addker_set_params(None, None, 1.0) == native.ADDKER_EINVAL
     assert lib.addker_sync(None) == native.ADDKER_EINVAL
     assert lib.addker_set_precond(None, 1) == native.ADDKER_EINVAL
+    assert lib.addker_set_schedule(None, 256, 256, 0, 0) == native.ADDKER_EINVAL
 
 
 def test_product_path_has_no_cpu_fallback():

@@ -198,7 +198,8 @@ def test_autotune_keeps_results(torch_cuda, cfg, N, nrhs):
     assert info["chunk_spread"] in op.AUTOTUNE_CHUNKS
     assert all(t > 0 for t in times.values()) and all(t > 0 for t in op.autotune_spread_times.values())
     assert all(t > 0 for t in op.autotune_residency_times.values())
-    assert info["spread_blocks_per_sm"] in (0, 1, 2, 3)
+    assert info["spread_blocks_per_sm"] in (0, 1, 2, 3) and info["spread_tile"] in (0, 1)
+    assert all(t > 0 for t in op.autotune_tile_times.values())
     # the spread phase's entry for the joint winner repeats the joint timing
     assert op.autotune_spread_times[chosen] == times[chosen]
     for _ in range(3):
@@ -217,3 +218,25 @@ def test_device_rates_are_plausible(torch_cuda):
     for k in ("ffma_tflops", "ffma2_tflops"):
         assert 0.2 * bound < r[k] < 2.2 * bound, (k, r[k], bound)
     assert r["shared_atomic_gops"] > 0 and r["global_atomic_gops"] > 0
+
+
+@pytest.mark.parametrize("cfg,N", [("c1", 20000), ("c3", 20000)])
+def test_every_schedule_matches_the_oracle(torch_cuda, cfg, N):
+    """Both 3-D spread register tiles, reduced residency and other item sizes (addker_set_schedule) give the
+    oracle's products: the schedule changes only the order of FP32 additions."""
+    torch = torch_cuda
+    wl = workloads.make(cfg, N=N)
+    v = wl.vector()
+    op = make_op(torch, wl)
+    Kr, dKr = fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f, v.astype(np.float64), wl.bandwidth,
+                                 wl.cutoff)
+    for chunk, chunk_sp, blocks, tile in [(256, 256, 0, 1), (128, 512, 2, 1), (512, 64, 1, 0), (256, 256, 0, 0)]:
+        op.set_schedule(chunk, chunk_sp, blocks, tile)
+        info = op.info()
+        assert (info["chunk"], info["chunk_spread"], info["spread_blocks_per_sm"], info["spread_tile"]) == \
+            (chunk, chunk_sp, blocks, tile)
+        Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
+        assert rel(Kv.cpu(), Kr) < TOL and rel(dK.cpu(), dKr) < TOL, (chunk, chunk_sp, blocks, tile)
+    from paper_2404_17344_gb300 import AddkerError
+    with pytest.raises(AddkerError):
+        op.set_schedule(256, 256, 0, 2)
