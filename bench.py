@@ -294,7 +294,7 @@ def run_ours(args, rank, world, local_rank):
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
 
     # measured FP32 and atomic rates of this device (after the timed region)
-    from paper_2404_17344_gb300 import device_rates
+    from paper_2404_17344_gb300.rates import device_rates
     rates = device_rates()
 
     # the spread's grid flush against the measured L2 atomic rate: one atomic add per box value (W^3) per

@@ -30,7 +30,7 @@
  *   gradients    addker_vjp (w^T K v with respect to v, ell, sigma_f and the points)
  *   solvers      addker_cg (regression system, Sec. 3.3), addker_gp_grad (GP training)
  *   analysis     addker_gsi (global sensitivity indices, Sec. 4)
- *   utilities    addker_prescale, addker_prescale_cube, addker_sync, addker_strerror, addker_device_rates, addker_profile,
+ *   utilities    addker_prescale, addker_prescale_cube, addker_sync, addker_strerror, addker_profile,
  *                addker_profile_read, addker_debug_stage
  * The additive Matern(1/2) kernel of Sec. 5 is selected by addker_opts.kernel.
  *
@@ -359,20 +359,6 @@ const char* addker_strerror(int status);
  */
 int addker_prescale(const float* X, int64_t N, int d, const int* win_off, const int* win_feat, int P,
                     double eps_B, float* Xs, double* factor, void* stream);
-
-/*
- * Device rates for roofline accounting (not in the paper; needs no plan). On the current device,
- * each rate from a kernel that does nothing else, median of 3 timed launches after a warm-up:
- *   out[0] SMs   out[1] SM clock under FP32 load, MHz (clock64 against the global timer)
- *   out[2] FFMA TFLOP/s   out[3] packed FFMA2 TFLOP/s (an FMA counts 2 flops)
- *   out[4] shared-memory float atomic adds, 10^9/s (distinct words)
- *   out[5] global float atomic adds into a 1 MiB L2-resident grid, 10^9/s (rows of 32 words)
- *   out[6] milliseconds of the FFMA launch
- *   out[7] global double atomic adds into a 2 MiB L2-resident grid, 10^9/s (rows of 32 words).
- * Writes up to `cap` values (host doubles) and returns the number available (8); synchronous,
- * about 0.2 s of GPU time. ADDKER_ECUDA / ADDKER_ENOMEM on failure.
- */
-int addker_device_rates(double* out, int cap);
 
 /*
  * Data prescaling of Sec. 3.2 in the paper's own two steps: every feature f is first mapped affinely

@@ -367,15 +367,3 @@ def prescale(X, windows, eps_B=1.0 / 16.0, rule="ball"):
                                            float(eps_B), ctypes.c_void_p(out.data_ptr()), ctypes.byref(f),
                                            _stream_ptr()), fn)
     return out, f.value
-
-
-def device_rates():
-    """Device rates for roofline accounting (addker_device_rates): a dict with the SM count, the SM
-    clock under FP32 load (MHz), FFMA and packed FFMA2 TFLOP/s, shared and global float atomic adds
-    (10^9/s, distinct words; the global ones into an L2-resident 1 MiB grid)."""
-    out = (ctypes.c_double * 8)()
-    n = native.lib().addker_device_rates(out, 8)
-    native.check(min(n, 0), "addker_device_rates")
-    keys = ("sms", "sm_mhz_under_load", "ffma_tflops", "ffma2_tflops", "shared_atomic_gops",
-            "global_atomic_gops", "ffma_launch_ms", "global_atomic64_gops")
-    return {k: float(out[i]) for i, k in enumerate(keys)}

@@ -14,7 +14,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libaddker.so")
-SOURCES = ["addker.cu", "fft.cu", "spread_gather.cu", "noalloc.cu", "gradients.cu", "solver.cu", "gsi.cu", "rates.cu"]
+SOURCES = ["addker.cu", "fft.cu", "spread_gather.cu", "noalloc.cu", "gradients.cu", "solver.cu", "gsi.cu"]
+RATES_SOURCE = "rates.cu"                 # the device-rate microbenchmark: its own library, not the product's
+RATES_LIB = os.path.join(OUT_DIR, "libaddker_rates.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", 
          "-Xptxas", "-v"]
@@ -30,14 +32,15 @@ def nvcc() -> str:
 def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     files.append(os.path.join(HERE, "..", "include", "addker.h"))
+    files.append(os.path.join(HERE, "..", "include", "addker_rates.h"))
     return files
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(LIB):
+    if not force and os.path.exists(LIB) and os.path.exists(RATES_LIB):
         newest = max(os.path.getmtime(f) for f in _deps())
-        if os.path.getmtime(LIB) >= newest:
+        if min(os.path.getmtime(LIB), os.path.getmtime(RATES_LIB)) >= newest:
             return LIB
     cc = nvcc()
     objs = []
@@ -54,8 +57,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stderr)
         return obj
 
-    with concurrent.futures.ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    with concurrent.futures.ThreadPoolExecutor(len(SOURCES) + 1) as ex:
+        objs = list(ex.map(compile_one, SOURCES + [RATES_SOURCE]))
+    rates_obj = objs.pop()
+    tmp_r = RATES_LIB + f".{os.getpid()}.tmp"
+    r = subprocess.run([cc, *ARCH, "-shared", rates_obj, "-o", tmp_r, "-lcudart"], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc link failed (rates):\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp_r, RATES_LIB)
     tmp = LIB + f".{os.getpid()}.tmp"
     r = subprocess.run([cc, *ARCH, "-shared", *objs, "-o", tmp, "-lcudart"], capture_output=True, text=True)
     if r.returncode != 0:

@@ -1,4 +1,5 @@
-// Device rates that bound the product's kernels (include/addker.h: addker_device_rates).
+// Device rates that bound the product's kernels (include/addker_rates.h: addker_device_rates), built into
+// its own library, libaddker_rates.so, apart from the product's.
 //
 // The spread and the gather of 3-D windows are bound by the FP32 FMA pipe and by how fast the
 // register tiles reach the grid (global atomic adds into an L2-resident grid); shared-memory atomics
@@ -14,6 +15,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "../../include/addker_rates.h"
 
 namespace {
 

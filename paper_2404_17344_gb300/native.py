@@ -64,7 +64,6 @@ SIGNATURES = {
     "addker_prescale": (_I, [_VP, _I64, _I, _VP, _VP, _I, _D, _VP, ctypes.POINTER(_D), _VP]),
     "addker_prescale_cube": (_I, [_VP, _I64, _I, _VP, _VP, _I, _D, _VP, ctypes.POINTER(_D), _VP]),
     "addker_info": (_I, [_VP, ctypes.POINTER(_I64), _I]),
-    "addker_device_rates": (_I, [ctypes.POINTER(_D), _I]),
     "addker_debug_stage": (_I, [_VP, _I, _I, _VP, _VP, _I64]),
     "addker_profile": (_I, [_VP, _I]),
     "addker_vjp": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),

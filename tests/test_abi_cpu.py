@@ -18,8 +18,8 @@ def lib():
     return native.lib()
 
 
-def declared_functions():
-    text = open(HEADER).read()
+def declared_functions(header=HEADER):
+    text = open(header).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(addker_[a-z_]+)\s*\(", text)))
 
@@ -34,6 +34,18 @@ def test_header_declares_the_boundary():
 def test_every_declared_symbol_is_exported(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
+
+
+def test_rate_library_is_apart_from_the_product(lib):
+    """The device-rate microbenchmark (include/addker_rates.h) is measurement tooling: its own library
+    exports it and the product library does not."""
+    from paper_2404_17344_gb300 import rates
+    names = declared_functions(os.path.join(ROOT, "include", "addker_rates.h"))
+    assert names == ["addker_device_rates"]
+    rl = rates.lib()
+    for name in names:
+        assert hasattr(rl, name), name
+        assert not hasattr(lib, name), name
 
 
 def test_binding_covers_header():

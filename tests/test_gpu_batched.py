@@ -211,7 +211,7 @@ def test_device_rates_are_plausible(torch_cuda):
     """addker_device_rates: every rate positive; the FP32 rates within the FMA pipe's bound
     (128 lanes per SM, 2 flops per FMA, at the measured clock; twice that for a packed
     FMA issued at full rate) up to timer noise."""
-    from paper_2404_17344_gb300 import device_rates
+    from paper_2404_17344_gb300.rates import device_rates
     r = device_rates()
     assert r["sms"] > 0 and r["sm_mhz_under_load"] > 100
     bound = r["sms"] * 128 * 2 * r["sm_mhz_under_load"] * 1e6 / 1e12
