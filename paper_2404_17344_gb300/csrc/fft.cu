@@ -51,14 +51,22 @@ __host__ __device__ inline void part_range(int pairs, int part, int* lo, int* hi
     *hi = min(pairs, *lo + per);
 }
 
+// Row strides that keep the second passes free of shared-memory bank conflicts: twiddle rows are read
+// by lanes that differ in the row index, so a row of M float2 (a multiple of 128 bytes) is padded by one
+// element; k_xround's tx region is rounded up to an even element count so the float4 arrays behind it
+// stay 16-byte aligned, and k_inv_yz keeps its z twiddles transposed, tzT[kz][z] with an even row length,
+// so that one float4 load gives the pair (z0, z0 + 1).
+__host__ __device__ inline int even_up(int n) { return n + (n & 1); }
+__host__ __device__ inline int xround_tx(int b0, int M) { return even_up(b0 * (M + 1)); }
+
 // Shared memory of the three kernels for one box (b0, b1, b2) and bandwidth M.
 __host__ __device__ inline void fused3_smem(int b0, int b1, int b2, int M, size_t* s)
 {
     const int kw = 2 * ((M / 2 + kSplit - 1) / kSplit);                 // kz columns per k_fwd_yz block
     const int ny = 2 * (((b1 + 1) / 2 + kSplit - 1) / kSplit);           // y rows per k_inv_yz block
     s[0] = sizeof(float2) * (b2 * kw + b1 * M + b1 * kw) + sizeof(float) * b1 * b2;
-    s[1] = sizeof(float2) * (b0 * M + b0 * kTile) + sizeof(float4) * M * kTile + 2 * sizeof(float) * M * kTile;
-    s[2] = sizeof(float4) * (M * M + ny * M) + sizeof(float2) * (ny + b2) * M;
+    s[1] = sizeof(float2) * (xround_tx(b0, M) + b0 * kTile) + sizeof(float4) * M * kTile + 2 * sizeof(float) * M * kTile;
+    s[2] = sizeof(float4) * (M * M + ny * M) + sizeof(float2) * (ny * (M + 1) + M * even_up(b2));
 }
 
 // block = (x-slab and kz part, window, rhs). smem: tz[b2][kw], ty[b1][M], t1[b1][kw] float2, gs[b1][b2].
@@ -136,7 +144,7 @@ __global__ void __launch_bounds__(kT3) k_fwd_yz(const WinDev* __restrict__ wins,
     }
 }
 
-// block = (tile of kTile columns c = (ky, kz), window, rhs). smem: tx[b0][M] float2, ts[b0][kTile]
+// block = (tile of kTile columns c = (ky, kz), window, rhs). smem: tx[b0][M + 1] float2, ts[b0][kTile]
 // float2, ss[M][kTile] float4, then the tile's multipliers mK[M][kTile], mD[M][kTile] (staged with
 // cp.async beside the tile rather than read from global memory inside the product loop).
 //   S[kx][c] = m_k sum_x tx[x][kx] t[x][c];   B[x][c] = sum_kx conj(tx[x][kx]) S[kx][c]
@@ -151,13 +159,14 @@ __global__ void __launch_bounds__(kT3) k_xround(const WinDev* __restrict__ wins,
     const int c0 = blockIdx.x * kTile;
     if (c0 >= MM) return;
     constexpr int JP = kTile / 2;                               // column pairs per tile
+    const int TXS = M + 1;                                      // padded row of tx
     float2* tx = reinterpret_cast<float2*>(smem);
-    float2* ts = tx + b0 * M;
+    float2* ts = tx + xround_tx(b0, M);
     float4* ss = reinterpret_cast<float4*>(ts + b0 * kTile);
     const int cols = min(kTile, MM - c0);                       // M^2 need not be a multiple of kTile
     const int r = blockIdx.z;                                  // right-hand-side slot
     const float2* t = reinterpret_cast<const float2*>(W.buf1 + r * W.b1sz);
-    for (int i = threadIdx.x; i < b0 * M; i += kT3) cp_async8(tx + i, W.twf[0] + i);
+    for (int i = threadIdx.x; i < b0 * M; i += kT3) cp_async8(tx + (i / M) * TXS + i % M, W.twf[0] + i);
     grid_dep_wait();
     for (int i = threadIdx.x; i < b0 * kTile; i += kT3) {
         const int x = i / kTile, j = i % kTile;
@@ -186,9 +195,8 @@ __global__ void __launch_bounds__(kT3) k_xround(const WinDev* __restrict__ wins,
         float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
 #pragma unroll 4
         for (int x = 0; x < b0; ++x) {
-            const float4 w = *reinterpret_cast<const float4*>(tx + x * M + kx);
+            const float2 w0 = tx[x * TXS + kx], w1 = tx[x * TXS + kx + 1];
             const float4 v = *reinterpret_cast<const float4*>(ts + x * kTile + j);
-            const float2 w0 = make_float2(w.x, w.y), w1 = make_float2(w.z, w.w);
             const float2 s0 = make_float2(v.x, v.y), s1 = make_float2(v.z, v.w);
             a00 = cmad(s0, w0, a00);
             a01 = cmad(s1, w0, a01);
@@ -220,7 +228,7 @@ __global__ void __launch_bounds__(kT3) k_xround(const WinDev* __restrict__ wins,
         float2 d00 = k00, d01 = k00, d10 = k00, d11 = k00;
 #pragma unroll 4
         for (int kx = 0; kx < M; ++kx) {
-            const float2 w0 = tx[x0 * M + kx], w1 = tx[x1 * M + kx];
+            const float2 w0 = tx[x0 * TXS + kx], w1 = tx[x1 * TXS + kx];
             const float4 s0 = ss[kx * kTile + j], s1 = ss[kx * kTile + j + 1];
             k00 = cmadc(make_float2(s0.x, s0.y), w0, k00);
             d00 = cmadc(make_float2(s0.z, s0.w), w0, d00);
@@ -243,8 +251,8 @@ __global__ void __launch_bounds__(kT3) k_xround(const WinDev* __restrict__ wins,
     }
 }
 
-// block = (x-slab and y part, window, rhs). smem: bs[M][M] float4, b1s[ny][M] float4, ty[ny][M],
-// tz[b2][M] float2, for the block's rows y = yb .. yb + ny - 1 (the last row repeated when b1 is odd):
+// block = (x-slab and y part, window, rhs). smem: bs[M][M] float4, b1s[ny][M] float4, ty[ny][M + 1],
+// tzT[M][even_up(b2)] float2, for the block's rows y = yb .. yb + ny - 1 (the last row repeated when b1 is odd):
 //   B1[y][kz] = sum_ky conj(ty[y][ky]) B[x][ky][kz];   h[x][y][z] = Re sum_kz conj(tz[z][kz]) B1[y][kz]
 // The block also zeroes its rows of the spread grid, which k_fwd_yz has consumed, so d = 3 grids
 // need no separate clearing before the next spread.
@@ -265,12 +273,16 @@ __global__ void __launch_bounds__(kT3) k_inv_yz(const WinDev* __restrict__ wins,
     const int MM = M * M;
     float4* bs = reinterpret_cast<float4*>(smem);
     float4* b1s = bs + MM;
+    const int TYS = M + 1, TZS = even_up(b2);                   // padded ty row; transposed tz row
     float2* ty = reinterpret_cast<float2*>(b1s + ny * M);
-    float2* tz = ty + ny * M;
+    float2* tzT = ty + ny * TYS;
     const int r = blockIdx.z;                                  // right-hand-side slot
     const float4* B = W.buf2 + r * W.b2sz + (size_t)x * MM;
-    for (int i = threadIdx.x; i < ny * M; i += kT3) cp_async8(ty + i, W.twf[1] + min(yb + i / M, b1 - 1) * M + i % M);
-    for (int i = threadIdx.x; i < b2 * M; i += kT3) cp_async8(tz + i, W.twf[2] + i);
+    for (int i = threadIdx.x; i < ny * M; i += kT3)
+        cp_async8(ty + (i / M) * TYS + i % M, W.twf[1] + min(yb + i / M, b1 - 1) * M + i % M);
+    for (int i = threadIdx.x; i < b2 * M; i += kT3) cp_async8(tzT + (i % M) * TZS + i / M, W.twf[2] + i);
+    if (b2 & 1)
+        for (int kz = threadIdx.x; kz < M; kz += kT3) tzT[kz * TZS + b2] = make_float2(0.f, 0.f);
     grid_dep_wait();
     for (int i = threadIdx.x; i < MM; i += kT3) cp_async16(bs + i, B + i);
     const int zrows = min(ny, b1 - yb);
@@ -285,13 +297,14 @@ __global__ void __launch_bounds__(kT3) k_inv_yz(const WinDev* __restrict__ wins,
     __syncthreads();
     const int Mh = M / 2;
     for (int o = threadIdx.x; o < nq * Mh; o += kT3) {            // 2x2 blocks (y, kz), local rows
-        const int y0 = 2 * (o / Mh), kz = 2 * (o % Mh);
+        // columns kz and kz + M/2, so the lanes of a row read one contiguous run of bs
+        const int y0 = 2 * (o / Mh), kz = o % Mh, kz1 = kz + Mh;
         float2 k00 = make_float2(0.f, 0.f), k01 = k00, k10 = k00, k11 = k00;
         float2 d00 = k00, d01 = k00, d10 = k00, d11 = k00;
 #pragma unroll 4
         for (int ky = 0; ky < M; ++ky) {
-            const float2 w0 = ty[y0 * M + ky], w1 = ty[(y0 + 1) * M + ky];
-            const float4 s0 = bs[ky * M + kz], s1 = bs[ky * M + kz + 1];
+            const float2 w0 = ty[y0 * TYS + ky], w1 = ty[(y0 + 1) * TYS + ky];
+            const float4 s0 = bs[ky * M + kz], s1 = bs[ky * M + kz1];
             k00 = cmadc(make_float2(s0.x, s0.y), w0, k00);
             d00 = cmadc(make_float2(s0.z, s0.w), w0, d00);
             k01 = cmadc(make_float2(s1.x, s1.y), w0, k01);
@@ -302,20 +315,21 @@ __global__ void __launch_bounds__(kT3) k_inv_yz(const WinDev* __restrict__ wins,
             d11 = cmadc(make_float2(s1.z, s1.w), w1, d11);
         }
         b1s[y0 * M + kz] = make_float4(k00.x, k00.y, d00.x, d00.y);
-        b1s[y0 * M + kz + 1] = make_float4(k01.x, k01.y, d01.x, d01.y);
+        b1s[y0 * M + kz1] = make_float4(k01.x, k01.y, d01.x, d01.y);
         b1s[(y0 + 1) * M + kz] = make_float4(k10.x, k10.y, d10.x, d10.y);
-        b1s[(y0 + 1) * M + kz + 1] = make_float4(k11.x, k11.y, d11.x, d11.y);
+        b1s[(y0 + 1) * M + kz1] = make_float4(k11.x, k11.y, d11.x, d11.y);
     }
     __syncthreads();
     float2* h = W.h + r * W.gsz + (size_t)x * b1 * b2;
     const int nb2 = (b2 + 1) / 2;
     for (int o = threadIdx.x; o < nq * nb2; o += kT3) {          // 2x2 blocks (y, z), local rows
         const int l0 = 2 * (o / nb2);
-        const int z0 = 2 * (o % nb2), z1 = min(z0 + 1, b2 - 1);
+        const int z0 = 2 * (o % nb2), z1 = z0 + 1;                // z1 = b2 reads the zero padding of tzT
         float k00 = 0.f, k01 = 0.f, k10 = 0.f, k11 = 0.f, d00 = 0.f, d01 = 0.f, d10 = 0.f, d11 = 0.f;
 #pragma unroll 4
         for (int kz = 0; kz < M; ++kz) {
-            const float2 w0 = tz[z0 * M + kz], w1 = tz[z1 * M + kz];
+            const float4 w = *reinterpret_cast<const float4*>(tzT + kz * TZS + z0);
+            const float2 w0 = make_float2(w.x, w.y), w1 = make_float2(w.z, w.w);
             const float4 s0 = b1s[l0 * M + kz], s1 = b1s[(l0 + 1) * M + kz];
             // Re(s conj(w)) = s.re w.re + s.im w.im
             k00 = fmaf(s0.x, w0.x, fmaf(s0.y, w0.y, k00));
