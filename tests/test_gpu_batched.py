@@ -10,6 +10,7 @@ import pytest
 
 import workloads
 from oracle import fastsum
+from parity_metrics import close
 
 pytestmark = pytest.mark.gpu
 
@@ -60,9 +61,9 @@ def test_batched_matches_single_and_oracle(torch_cuda, cfg, N, nrhs):
     for j in (0, nrhs - 1):                      # first chunk and last (possibly partial) chunk
         Kr, dKr = fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f,
                                      V[:, j].cpu().numpy().astype(np.float64), wl.bandwidth, wl.cutoff)
-        assert rel(Kv[:, j].cpu(), Kr) < TOL
+        assert close(Kv[:, j].cpu(), Kr)
         for s in range(wl.P):
-            assert rel(dK[s, :, j].cpu(), dKr[s]) < TOL, (j, s)
+            assert close(dK[s, :, j].cpu(), dKr[s]), (j, s)
 
 
 def test_batched_selectors_mixed_windows(torch_cuda):
@@ -108,7 +109,7 @@ def test_batched_generic_cutoff(torch_cuda):
     assert rel(Kv.cpu(), K1) < TOL and rel(dK.cpu(), D1) < TOL
     Kr, dKr = fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f, V[:, 4].cpu().numpy().astype(np.float64),
                                  wl.bandwidth, wl.cutoff)
-    assert rel(Kv[:, 4].cpu(), Kr) < TOL and rel(dK[:, :, 4].cpu(), dKr) < TOL
+    assert close(Kv[:, 4].cpu(), Kr) and close(dK[:, :, 4].cpu(), dKr)
 
 
 def test_largest_small_transform(torch_cuda):
@@ -124,7 +125,7 @@ def test_largest_small_transform(torch_cuda):
     for j in range(2):
         Kr, dKr = fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f,
                                      V[:, j].cpu().numpy().astype(np.float64), wl.bandwidth, wl.cutoff)
-        assert rel(Kv[:, j].cpu(), Kr) < TOL and rel(dK[:, :, j].cpu(), dKr) < TOL
+        assert close(Kv[:, j].cpu(), Kr) and close(dK[:, :, j].cpu(), dKr)
 
 
 def test_host_entry_batched(torch_cuda):
@@ -236,7 +237,7 @@ def test_every_schedule_matches_the_oracle(torch_cuda, cfg, N):
         assert (info["chunk"], info["chunk_spread"], info["spread_blocks_per_sm"], info["spread_tile"]) == \
             (chunk, chunk_sp, blocks, tile)
         Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
-        assert rel(Kv.cpu(), Kr) < TOL and rel(dK.cpu(), dKr) < TOL, (chunk, chunk_sp, blocks, tile)
+        assert close(Kv.cpu(), Kr) and close(dK.cpu(), dKr), (chunk, chunk_sp, blocks, tile)
     from paper_2404_17344_gb300 import AddkerError
     with pytest.raises(AddkerError):
         op.set_schedule(256, 256, 0, 2)

@@ -9,6 +9,7 @@ import pytest
 
 import workloads
 from oracle import _clib, fastsum, window
+from parity_metrics import close
 
 pytestmark = pytest.mark.gpu
 
@@ -66,10 +67,10 @@ def test_compensated_products_match_oracle(torch_cuda, cfg, N, cutoff, nrhs):
     vj = (V[:, j] if nrhs > 1 else V).astype(np.float64)
     Kr, dKr = fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f, vj, wl.bandwidth, wl.cutoff)
     Kg = Kv[:, j] if nrhs > 1 else Kv
-    assert rel(Kg.cpu(), Kr) < TOL
+    assert close(Kg.cpu(), Kr)
     for s in range(wl.P):
         Dg = dK[s, :, j] if nrhs > 1 else dK[s]
-        assert rel(Dg.cpu(), dKr[s]) < TOL, s
+        assert close(Dg.cpu(), dKr[s]), s
     # repeated products: the FP64 grids are cleared by every transform, so nothing carries over; what
     # differs between two products is only the order of FP32 adds inside a work item where a kernel
     # accumulates its box with shared-memory atomics (the generic kernels: measured 5e-9 - 1e-7)

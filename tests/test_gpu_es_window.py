@@ -9,6 +9,7 @@ import pytest
 
 import workloads
 from oracle import _clib, fastsum, window
+from parity_metrics import close
 
 pytestmark = pytest.mark.gpu
 
@@ -47,7 +48,7 @@ def test_es_products_match_oracle(torch_cuda, cfg, N):
     Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
     Kr, dKr = fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f, v.astype(np.float64), wl.bandwidth,
                                  wl.cutoff, win="es")
-    assert rel(Kv.cpu(), Kr) < TOL
+    assert close(Kv.cpu(), Kr)
     # with one point the derivative products vanish (kappa_der(0) = 0): measure against |K v| there
     den = lambda b: max(np.linalg.norm(b), np.linalg.norm(Kr) if N == 1 else 0.0)
     for s in range(wl.P):
@@ -71,7 +72,7 @@ def test_es_spread_grid_matches_oracle(torch_cuda):
     v64 = v.astype(np.float64)                                  # kept alive across the call
     _clib.lib().orc_spread(len(x), 3, _clib.ptr(x), _clib.ptr(v64), n, wl.cutoff,
                            window.es_beta(wl.cutoff), window.KINDS["es"], _clib.ptr(gref))
-    assert rel(np.asarray(g).reshape(gref.shape), gref) < TOL
+    assert close(np.asarray(g).reshape(gref.shape), gref)
 
 
 def test_es_and_kb_approach_the_same_sum(torch_cuda):
@@ -110,6 +111,6 @@ def test_es_window_with_other_options(torch_cuda, kernel, comp):
     Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
     Kr, dKr = fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f, v.astype(np.float64), wl.bandwidth,
                                  wl.cutoff, win="es", kernel=kernel)
-    assert rel(Kv.cpu(), Kr) < TOL
+    assert close(Kv.cpu(), Kr)
     for s in range(wl.P):
-        assert rel(dK[s].cpu(), dKr[s]) < TOL, s
+        assert close(dK[s].cpu(), dKr[s]), s

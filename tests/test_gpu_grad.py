@@ -10,6 +10,7 @@ import pytest
 
 import workloads
 from oracle import gradients
+from parity_metrics import close
 
 pytestmark = pytest.mark.gpu
 
@@ -47,10 +48,10 @@ def test_vjp_vs_oracle_nfft_gradients(torch_cuda, cfg, N):
     gv, gt, gx = op.vjp(torch.from_numpy(v).cuda(), torch.from_numpy(w).cuda())
     rv, rell, rsf, rx = gradients.nfft_grad(wl.points, wl.windows, wl.ell, wl.sigma_f, v, w, wl.bandwidth, wl.cutoff)
     gt = gt.cpu().numpy()
-    assert rel(gv.cpu(), rv) < TOL
-    assert rel(gt[:wl.P], rell) < TOL
+    assert close(gv.cpu(), rv)
+    assert close(gt[:wl.P], rell)
     assert abs(gt[wl.P] - rsf) <= TOL * abs(rsf)
-    assert rel(gx.cpu(), rx) < TOL_X
+    assert close(gx.cpu(), rx, TOL_X)
 
 
 def test_autograd_function_matches_oracle(torch_cuda):
@@ -66,10 +67,10 @@ def test_autograd_function_matches_oracle(torch_cuda):
     loss = (torch.from_numpy(w).cuda() * y).sum()
     loss.backward()
     rv, rell, rsf, rx = gradients.nfft_grad(wl.points, wl.windows, wl.ell, 1.2, v, w, wl.bandwidth, wl.cutoff)
-    assert rel(vt.grad.cpu(), rv) < TOL
-    assert rel(ell.grad.cpu(), rell) < TOL
+    assert close(vt.grad.cpu(), rv)
+    assert close(ell.grad.cpu(), rell)
     assert abs(float(sf.grad) - rsf) <= TOL * abs(rsf)
-    assert rel(X.grad.cpu(), rx) < TOL_X
+    assert close(X.grad.cpu(), rx, TOL_X)
 
 
 def test_finite_differences_on_gpu(torch_cuda):
@@ -137,7 +138,7 @@ def test_vjp_at_the_configuration_size(torch_cuda):
     gv, gt, gx = op.vjp(torch.from_numpy(v).cuda(), torch.from_numpy(w).cuda())
     gv, gt, gx = gv.cpu().numpy(), gt.cpu().numpy(), gx.cpu().numpy()
     rv, rell, rsf, rx = gradients.nfft_grad(wl.points, wl.windows, wl.ell, wl.sigma_f, v, w, wl.bandwidth, wl.cutoff)
-    assert rel(gv, rv) < TOL
-    assert rel(gt[:wl.P], rell) < TOL
+    assert close(gv, rv)
+    assert close(gt[:wl.P], rell)
     assert abs(gt[wl.P] - rsf) <= TOL * abs(rsf)
-    assert rel(gx, rx) < TOL_X
+    assert close(gx, rx, TOL_X)
