@@ -241,6 +241,26 @@ def test_edge_cases(torch_cuda):
     assert close(Kv.cpu(), Kr) and close(dK.cpu(), dKr)
 
 
+def test_points_on_grid_lines(torch_cuda):
+    """Coordinates on the oversampled grid's lines (n x an integer: the window taken at the end of its
+    polynomial pieces, the cell index exactly at a step of floor) and on cell centres, every third point
+    repeated; a 3-D window (fast kernels) and a 1-D window (low-dimensional kernels) at M = 32, n = 64."""
+    torch = torch_cuda
+    rng = np.random.default_rng(11)
+    k = rng.integers(-7, 8, size=(600, 4)).astype(np.float64)
+    half = 0.5 * rng.integers(0, 2, size=(600, 4))
+    X = ((k + half) / 64.0).astype(np.float32)
+    X = np.concatenate([X, X[::3]])
+    wl = workloads.Workload("lines", X, [(0, 1, 2), (3,)], np.array([0.3, 0.5]), 1.0, [32, 32], 4, 5)
+    v = wl.vector()
+    op = make_op(torch, wl)
+    Kv, dK = op.matvec_all(torch.from_numpy(v).cuda())
+    Kr, dKr = oracle_all(wl, v)
+    assert close(Kv.cpu(), Kr)
+    for s in range(wl.P):
+        assert close(dK[s].cpu(), dKr[s]), s
+
+
 def test_rejects_point_outside_ball(torch_cuda):
     torch = torch_cuda
     from paper_2404_17344_gb300 import AddKer, AddkerError
