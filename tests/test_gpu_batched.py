@@ -128,6 +128,30 @@ def test_largest_small_transform(torch_cuda):
         assert close(Kv[:, j].cpu(), Kr) and close(dK[:, :, j].cpu(), dKr)
 
 
+def test_host_entry_pageable_buffers(torch_cuda):
+    """addker_matvec_all_host with ordinary (pageable) host memory and three right-hand sides: the copies go
+    through cudaMemcpyAsync instead of the copy kernels of page-locked buffers; results as on device
+    buffers and against the oracle."""
+    torch = torch_cuda
+    wl = workloads.make("c1", N=3000)
+    nrhs = 3
+    v = wl.vector(nrhs=nrhs)
+    op = make_op(torch, wl)
+    Kd, dKd = op.matvec_all(torch.from_numpy(v).cuda())
+    vh = torch.from_numpy(np.ascontiguousarray(v.T)).reshape(-1)
+    Kh = torch.empty(wl.N * nrhs)
+    dKh = torch.empty(wl.N * wl.P * nrhs)
+    assert not vh.is_pinned() and not Kh.is_pinned()
+    op.matvec_all_host(vh, Kh, dKh, nrhs)
+    assert rel(Kh.reshape(nrhs, wl.N).t(), Kd.cpu()) < TOL
+    assert rel(dKh.reshape(nrhs, wl.P, wl.N).permute(1, 2, 0), dKd.cpu()) < TOL
+    Kr, dKr = fastsum.matvec_all(wl.points, wl.windows, wl.ell, wl.sigma_f, v[:, 2].astype(np.float64),
+                                 wl.bandwidth, wl.cutoff)
+    assert close(Kh.reshape(nrhs, wl.N)[2], Kr)
+    for s in range(wl.P):
+        assert close(dKh.reshape(nrhs, wl.P, wl.N)[2, s], dKr[s]), s
+
+
 def test_host_entry_batched(torch_cuda):
     torch = torch_cuda
     wl = workloads.make("c3", N=2000)

@@ -192,7 +192,7 @@ def test_host_buffers_entry_full_size_against_the_oracle(torch_cuda):
     Kh = torch.empty(wl.N).pin_memory()
     dKh = torch.empty(wl.N * wl.P).pin_memory()
     op.matvec_all_host(vh, Kh, dKh)
-    op.matvec_all_host(vh, Kh, dKh)                   # the second call replays a captured graph
+    op.matvec_all_host(vh, Kh, dKh)                   # the second call runs on the staging buffers the first made
     Kh, dKh = Kh.numpy(), dKh.numpy().reshape(wl.P, wl.N)
     rows = np.random.default_rng(11).choice(wl.N, 4096, replace=False)
     Kn, dKn = oracle_all(wl, v, rows=rows)
