@@ -128,6 +128,25 @@ def test_largest_small_transform(torch_cuda):
         assert close(Kv[:, j].cpu(), Kr) and close(dK[:, :, j].cpu(), dKr)
 
 
+def test_products_on_a_side_stream(torch_cuda):
+    """addker_set_stream: the binding hands the library torch's current stream before every call. Products
+    issued on a side stream (three in a row, so the repeated ones run as replayed graphs there) equal those
+    of the default stream, and are complete once that stream is synchronised."""
+    torch = torch_cuda
+    wl = workloads.make("c3", N=2500)
+    V = torch.from_numpy(wl.vector(nrhs=3)).cuda()
+    op = make_op(torch, wl)
+    K0, D0 = op.matvec_all(V)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        outs = [op.matvec_all(V) for _ in range(3)]
+    side.synchronize()
+    for k, d in outs:
+        assert rel(k.cpu(), K0.cpu()) < TOL and rel(d.cpu(), D0.cpu()) < TOL
+
+
 def test_host_entry_pageable_buffers(torch_cuda):
     """addker_matvec_all_host with ordinary (pageable) host memory and three right-hand sides: the copies go
     through cudaMemcpyAsync instead of the copy kernels of page-locked buffers; results as on device
